@@ -1,0 +1,89 @@
+"""Invariants of the oracle's index construction (Alg. 1-3, Sec. 4.2).
+
+Parity of the construction itself is unpinned (no reference graph exists);
+these tests check what the paper states the graph must satisfy.
+"""
+from collections import deque
+
+import numpy as np
+
+import oracle
+
+NONE = 0xFFFFFFFF
+
+
+def _lists(adj):
+    return [[int(u) for u in row if u != NONE] for row in adj]
+
+
+def test_degree_bounds_no_self_loops_no_duplicates(tiny):
+    M = tiny["M"]
+    pj, fin = _lists(tiny["pj"]), _lists(tiny["adj"])
+    for v, (a, b) in enumerate(zip(pj, fin)):
+        assert len(a) <= M and len(b) <= 2 * M
+        assert v not in a and v not in b
+        assert len(set(a)) == len(a) and len(set(b)) == len(b)
+        # padding only at the end of a row
+        row = tiny["adj"][v]
+        assert np.all(row[len(b):] == NONE)
+
+
+def test_every_node_reachable_from_entry(tiny):
+    fin = _lists(tiny["adj"])
+    seen = np.zeros(len(fin), bool)
+    seen[tiny["entry"]] = True
+    dq = deque([tiny["entry"]])
+    while dq:
+        v = dq.popleft()
+        for u in fin[v]:
+            if not seen[u]:
+                seen[u] = True
+                dq.append(u)
+    assert seen.all()
+
+
+def test_projection_edges_come_from_bipartite_candidates(tiny):
+    """Every G_pj edge a->b links a pivot to a node reached through one of
+    its bridge queries (Alg. 2 lines 3-5), either forward (b in U(a)) or as
+    the reverse edge of a pivot b (a in U(b))."""
+    knn = tiny["knn"]
+    n = tiny["X"].shape[0]
+    U = [set() for _ in range(n)]
+    for t in range(knn.shape[0]):
+        U[int(knn[t, 0])].update(int(c) for c in knn[t, 1:])
+    for a, row in enumerate(_lists(tiny["pj"])):
+        for b in row:
+            assert b in U[a] or a in U[b]
+
+
+def test_final_lists_start_with_projection_lists(tiny):
+    pj, fin = _lists(tiny["pj"]), _lists(tiny["adj"])
+    for a, b in zip(pj, fin):
+        assert b[:len(a)] == a
+    assert tiny["stats"]["repairs"] >= (1 if tiny["stats"]["unreachable_before_repair"] else 0)
+
+
+def test_pivots_are_the_1nn_of_some_training_query(tiny):
+    knn = tiny["knn"]
+    assert tiny["stats"]["pivots"] == len(set(knn[:, 0].tolist()))
+
+
+def test_recall_non_decreasing_in_L(tiny):
+    X, Q, gt = tiny["X"], tiny["Q"], tiny["gt"]
+    rec = []
+    for L in (10, 20, 50, 100):
+        ids, *_ = oracle.beam_search(X, tiny["adj"], tiny["entry"], Q, 10, L)
+        rec.append(oracle.recall_at_k(ids, gt, 10))
+    assert all(b >= a for a, b in zip(rec, rec[1:])), rec
+    assert rec[-1] > 0.6
+
+
+def test_tiny_search_reaches_exact_result_at_full_L(tiny):
+    """L >= N on the connected final graph gives the exact top-k (Sec. 4.3)."""
+    X, Q = tiny["X"], tiny["Q"][:3]
+    ids, dist, visits, *_ = oracle.beam_search(X, tiny["adj"], tiny["entry"], Q, 10, X.shape[0])
+    for i in range(len(Q)):
+        dd = np.array([-oracle.dot_fixed(Q[i], x) for x in X], np.float32)
+        order = np.lexsort((np.arange(len(X)), dd))[:10]
+        assert ids[i].tolist() == order.tolist()
+    assert np.all(visits == X.shape[0])

@@ -1,0 +1,84 @@
+"""Pins for the oracle's beam search (Sec. 4.3)."""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import load_golden, path_graph
+
+NONE = 0xFFFFFFFF
+
+
+def test_hand_traced_path_graph():
+    g = load_golden("beam_path6.json")
+    X, adj = path_graph(g["a"])
+    q = np.array([1, 0, 0, 0], np.float32)
+    for c in g["cases"]:
+        pid, pdist, trace, visits, hops, st = oracle.beam_search_trace(
+            X, adj, g["entry"], q, c["L"], c["max_visits"])
+        assert trace.tolist() == c["trace"], c
+        assert pid.tolist() == c["pool_ids"]
+        assert pdist.tolist() == c["pool_dist"]
+        assert (visits, hops, st) == (c["visits"], c["hops"], c["status"])
+
+
+def _exact_topk_fixed(X, q, k):
+    dist = np.array([-oracle.dot_fixed(q, x) for x in X], np.float32)
+    order = np.lexsort((np.arange(len(X)), dist))
+    return order[:k], dist[order[:k]]
+
+
+def test_complete_graph_gives_exact_topk():
+    rng = np.random.default_rng(21)
+    n, d = 40, 16
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    adj = np.array([[u for u in range(n) if u != v] for v in range(n)], np.uint32)
+    Q = rng.standard_normal((10, d)).astype(np.float32)
+    ids, dist, visits, hops, st = oracle.beam_search(X, adj, 7, Q, 5, 5)
+    for i in range(len(Q)):
+        ref_ids, ref_d = _exact_topk_fixed(X, Q[i], 5)
+        assert ids[i].tolist() == ref_ids.tolist()
+        assert np.array_equal(dist[i], ref_d)
+    assert np.all(visits == n) and np.all(st == 0)
+
+
+def test_large_L_on_connected_graph_is_exact():
+    rng = np.random.default_rng(22)
+    n, d, r = 300, 8, 6
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    adj = np.full((n, r), NONE, np.uint32)
+    for v in range(n):                      # ring plus random chords: connected
+        nb = {(v + 1) % n, (v - 1) % n} | set(rng.integers(0, n, 3).tolist())
+        nb.discard(v)
+        nb = sorted(nb)[:r]
+        adj[v, :len(nb)] = nb
+    Q = rng.standard_normal((12, d)).astype(np.float32)
+    ids, dist, visits, hops, st = oracle.beam_search(X, adj, 0, Q, 10, n)
+    for i in range(len(Q)):
+        assert ids[i].tolist() == _exact_topk_fixed(X, Q[i], 10)[0].tolist()
+    assert np.all(visits == n) and np.all(hops == n)
+
+
+def test_padding_when_reachable_set_is_small():
+    X, adj = path_graph([0, 1, 3, 2, 5, 4])
+    adj[2, :] = NONE        # cut the path after node 2: only {0, 1, 2} reachable
+    q = np.array([[1, 0, 0, 0]], np.float32)
+    ids, dist, visits, hops, st = oracle.beam_search(X, adj, 0, q, 5, 8)
+    assert ids[0].tolist() == [2, 1, 0, NONE, NONE]
+    assert np.isinf(dist[0, 3:]).all() and dist[0, :3].tolist() == [-3.0, -1.0, -0.0]
+    assert visits[0] == 3 and hops[0] == 3
+
+
+def test_ties_broken_by_lower_id():
+    X = np.array([[0, 0, 0, 0], [2, 0, 0, 0], [2, 0, 0, 0], [1, 0, 0, 0], [2, 0, 0, 0]], np.float32)
+    adj = np.array([[4, 3, 2, 1]] + [[0, NONE, NONE, NONE]] * 4, np.uint32)
+    ids, dist, *_ = oracle.beam_search(X, adj, 0, np.array([[1, 0, 0, 0]], np.float32), 3, 3)
+    assert ids[0].tolist() == [1, 2, 4]
+
+
+def test_rejects_bad_arguments():
+    X, adj = path_graph([0, 1, 2])
+    q = np.zeros((1, 4), np.float32)
+    with pytest.raises(ValueError):
+        oracle.beam_search(X, adj, 5, q, 1, 1)       # entry out of range
+    with pytest.raises(ValueError):
+        oracle.beam_search(X, adj, 0, q, 3, 2)       # k > L
