@@ -1,0 +1,142 @@
+/*
+ * roargraph.h -- C ABI of the GB300 RoarGraph search library.
+ *
+ * RoarGraph (PVLDB 17(11), 2024) answers top-k maximum-inner-product queries
+ * (Definition 1, Sec. 2.1.1) by beam search over a graph index built from a
+ * query-base bipartite graph (Sec. 4.2). This library runs that search on the
+ * GPU, plus the dense step of the index build.
+ *
+ * Conventions shared by every call:
+ *  - All vectors are row-major FP32 unless stated; d must be a multiple of 4
+ *    (rows start on 16-byte boundaries) and at most 1024.
+ *  - delta(q, x) = -<q, x> (Sec. 5.1, MIPS); smaller is closer. Results are
+ *    ordered by (distance ascending, id ascending).
+ *  - Pointers marked "device" are CUDA device (or managed) memory; they are
+ *    borrowed, never freed by the library, and must outlive every call that
+ *    uses them (for an index: until roar_index_destroy returns).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls that
+ *    take a stream only enqueue work; the return code reports argument
+ *    validation and launch errors. Per-query outcomes go to `qstatus`.
+ *  - No call aborts, throws or traps. Errors return a roar_status; the text of
+ *    the last CUDA error is available from roar_last_error().
+ */
+#ifndef ROARGRAPH_H
+#define ROARGRAPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ROAR_OK = 0,
+    ROAR_EINVAL = 1,    /* bad argument (checked before any launch) */
+    ROAR_ENOMEM = 2,    /* device or host allocation failed */
+    ROAR_ECUDA = 3,     /* a CUDA call failed; see roar_last_error() */
+    ROAR_EOVERFLOW = 4, /* per query: the visit cap ended the search early */
+    ROAR_ETIMEOUT = 5,  /* a bounded wait gave up */
+    ROAR_EBUSY = 6      /* resource in use (e.g. a server slot table is full) */
+} roar_status;
+
+typedef enum {
+    ROAR_F32 = 0,       /* traversal on the FP32 rows themselves */
+    ROAR_BF16 = 1,      /* traversal on a BF16 copy, FP32 re-rank */
+    ROAR_FP8_E4M3 = 2   /* traversal on an FP8-E4M3 copy with per-row scales, FP32 re-rank */
+} roar_dtype;
+
+#define ROAR_NONE_ID 0xFFFFFFFFu   /* adjacency padding and unfilled result slots */
+#define ROAR_MAX_RMAX 128          /* largest adjacency row width */
+#define ROAR_MAX_L 1024            /* largest beam width (pool capacity) */
+#define ROAR_MAX_K ROAR_MAX_L
+
+typedef struct roar_index roar_index;
+
+/* Text for a status code (static storage). */
+const char *roar_status_string(roar_status s);
+
+/* Text of the last CUDA error seen by this thread (static storage, "" if none). */
+const char *roar_last_error(void);
+
+/*
+ * Create a search handle over a resident index (Sec. 4.3: "the medoid of the
+ * base data as the initial node").
+ *   n, d          base rows and dimension (1 <= n < 2^31, d % 4 == 0, d <= 1024).
+ *   base_f32      device [n][d] FP32 base vectors X. Required: the FP32 search
+ *                 traverses it, the reduced-precision forms re-rank with it.
+ *   trav_dtype    which copy the traversal reads (roar_dtype).
+ *   base_trav     device [n][d] BF16 (uint16) or FP8-E4M3 (uint8) copy; NULL
+ *                 for ROAR_F32. Produce it with roar_quantize.
+ *   scales        device [n] FP32 per-row scales for ROAR_FP8_E4M3, else NULL.
+ *   adj           device [n][rmax] uint32 out-neighbour ids, each row padded at
+ *                 its end with ROAR_NONE_ID (the RoarGraph index of Alg. 1).
+ *   rmax          row width, 1..ROAR_MAX_RMAX.
+ *   entry         entry node id (< n), normally the medoid.
+ *   max_visits    per-query cap on distinct visited nodes (0 = 16384, max 2^24);
+ *                 sizes the library's scratch (see below).
+ *   out           receives the handle.
+ * Scratch: a 4-byte work counter at creation; on the first search that needs
+ * them, one overflow visited table per resident warp of
+ * next_pow2(2*(max_visits+rmax)) 8-byte slots (growing them synchronises the
+ * device, so run one search before capturing searches in a CUDA graph).
+ * Searches on one handle must not overlap in time (enqueue them on one
+ * stream); create one handle per concurrent stream.
+ * Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ */
+roar_status roar_index_create(int64_t n, int32_t d, const float *base_f32, roar_dtype trav_dtype,
+                              const void *base_trav, const float *scales, const uint32_t *adj,
+                              int32_t rmax, uint32_t entry, uint32_t max_visits, roar_index **out);
+
+/* Release a handle and its scratch (synchronises the device first). NULL is ignored. */
+void roar_index_destroy(roar_index *idx);
+
+/*
+ * Tuning: shared-memory visited-table capacity 2^log2 slots per query
+ * (5 <= log2 <= 15), or 0 to choose from L automatically. A query that
+ * visits more than half the table continues in its exact overflow table, so
+ * results never depend on this setting; speed and occupancy do.
+ * Errors: ROAR_EINVAL.
+ */
+roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2);
+
+/*
+ * Beam search (Sec. 4.3) of nq queries, each owned by one warp: start from
+ * the entry, repeatedly expand the closest unexpanded pool entry, score its
+ * unvisited out-neighbours, keep the first L under (distance, id), stop when
+ * every pool entry is expanded. For ROAR_BF16 / ROAR_FP8_E4M3 handles the
+ * traversal uses the reduced-precision copy, then every pool entry is
+ * re-scored in FP32 and the first k of the re-sorted pool are returned.
+ * FP32 distances use one fixed summation order (element i to lane
+ * (i>>2)&31, fmaf per lane, then an xor butterfly 16,8,4,2,1), so results
+ * are deterministic and independent of batch composition.
+ *   queries   device [nq][d] FP32.
+ *   k, L      1 <= k <= L <= ROAR_MAX_L.
+ *   ids       device [nq][k] uint32 out; unfilled slots ROAR_NONE_ID.
+ *   dist      device [nq][k] FP32 out (-<q,x>); unfilled slots +inf.
+ *   visits    device [nq] uint32 out (distinct nodes scored), or NULL.
+ *   hops      device [nq] uint32 out (expansions), or NULL.
+ *   qstatus   device [nq] int32 out: ROAR_OK, ROAR_EOVERFLOW (visit cap hit;
+ *             the pool so far is returned) or ROAR_EINVAL (the graph holds an
+ *             id >= n, which is skipped); or NULL.
+ * nq == 0 is a no-op. Errors: ROAR_EINVAL, ROAR_ECUDA.
+ */
+roar_status roar_search(roar_index *idx, const float *queries, int64_t nq, int32_t k, int32_t L,
+                        uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops,
+                        int32_t *qstatus, void *stream);
+
+/*
+ * roar_search with HOST buffers: copies the queries in, searches, copies the
+ * results out and waits for completion before returning. Pinned host memory
+ * gives the fastest copies. The device staging buffers are owned by the
+ * handle and grow on demand. Same arguments and errors as roar_search.
+ */
+roar_status roar_search_host(roar_index *idx, const float *queries_host, int64_t nq, int32_t k,
+                             int32_t L, uint32_t *ids_host, float *dist_host,
+                             uint32_t *visits_host, uint32_t *hops_host, int32_t *qstatus_host,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROARGRAPH_H */

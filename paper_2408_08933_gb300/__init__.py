@@ -1,0 +1,174 @@
+"""GB300-native RoarGraph search: Python binding of libroargraph (include/roargraph.h).
+
+The binding only marshals arguments: every step of the search, the build's
+dense step and the quantisers run in the library's CUDA kernels. PyTorch
+provides device memory and streams. There is no CPU fallback: if the library
+is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build_ext
+
+NONE_ID = 0xFFFFFFFF
+ROAR_OK, ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA, ROAR_EOVERFLOW, ROAR_ETIMEOUT, ROAR_EBUSY = range(7)
+ROAR_F32, ROAR_BF16, ROAR_FP8_E4M3 = 0, 1, 2
+DTYPE_CODES = {"f32": ROAR_F32, "bf16": ROAR_BF16, "fp8": ROAR_FP8_E4M3}
+
+_lib = None
+
+
+class RoarError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib_ = _lib
+        msg = lib_.roar_status_string(status).decode() if lib_ else str(status)
+        detail = lib_.roar_last_error().decode() if lib_ else ""
+        super().__init__(f"{where}: {msg} ({detail})")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load libroargraph.so (built by ``build_ext.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(build_ext.LIB):
+        raise RuntimeError(f"libroargraph is not built ({build_ext.LIB} missing); "
+                           "run __graft_entry__.build() first")
+    L = ctypes.CDLL(build_ext.LIB)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    L.roar_status_string.argtypes = [ctypes.c_int]
+    L.roar_status_string.restype = ctypes.c_char_p
+    L.roar_last_error.argtypes = []
+    L.roar_last_error.restype = ctypes.c_char_p
+    L.roar_index_create.argtypes = [i64, i32, P, ctypes.c_int, P, P, P, i32, u32, u32,
+                                    ctypes.POINTER(P)]
+    L.roar_index_create.restype = ctypes.c_int
+    L.roar_index_set_hash_log2.argtypes = [P, i32]
+    L.roar_index_set_hash_log2.restype = ctypes.c_int
+    L.roar_index_destroy.argtypes = [P]
+    L.roar_index_destroy.restype = None
+    L.roar_search.argtypes = [P, P, i64, i32, i32, P, P, P, P, P, P]
+    L.roar_search.restype = ctypes.c_int
+    L.roar_search_host.argtypes = [P, P, i64, i32, i32, P, P, P, P, P, P]
+    L.roar_search_host.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != ROAR_OK:
+        raise RoarError(st, where)
+
+
+def roar_index_create(n, d, base_f32, trav_dtype, base_trav, scales, adj, rmax, entry,
+                      max_visits=0):
+    """Raw C-ABI call; pointer arguments are integers (device addresses) or None."""
+    h = ctypes.c_void_p()
+    _check(lib().roar_index_create(n, d, base_f32, trav_dtype, base_trav, scales, adj, rmax,
+                                   entry, max_visits, ctypes.byref(h)), "roar_index_create")
+    return h.value
+
+
+def roar_index_set_hash_log2(handle, log2):
+    _check(lib().roar_index_set_hash_log2(handle, log2), "roar_index_set_hash_log2")
+
+
+def roar_index_destroy(handle):
+    lib().roar_index_destroy(handle)
+
+
+def roar_search(handle, queries, nq, k, L, ids, dist, visits=None, hops=None, qstatus=None,
+                stream=None):
+    _check(lib().roar_search(handle, queries, nq, k, L, ids, dist, visits, hops, qstatus, stream),
+           "roar_search")
+
+
+def roar_search_host(handle, queries, nq, k, L, ids, dist, visits=None, hops=None, qstatus=None,
+                     stream=None):
+    _check(lib().roar_search_host(handle, queries, nq, k, L, ids, dist, visits, hops, qstatus,
+                                  stream), "roar_search_host")
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream_ptr(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Index:
+    """A resident index over torch CUDA tensors (kept alive by this object).
+
+    base_f32: float32 [n, d]; adj: int32/uint32-compatible [n, rmax] (stored as
+    int32 holding uint32 bits, padding -1 == 0xFFFFFFFF); trav: optional BF16
+    (int16/uint16 bits or torch.bfloat16) or FP8 (uint8) copy; scales: float32 [n].
+    """
+
+    def __init__(self, base_f32, adj, entry, dtype="f32", trav=None, scales=None, max_visits=0):
+        import torch
+
+        assert base_f32.is_cuda and base_f32.dtype == torch.float32 and base_f32.is_contiguous()
+        assert adj.is_cuda and adj.dtype == torch.int32 and adj.is_contiguous()
+        self.base_f32, self.adj, self.trav, self.scales = base_f32, adj, trav, scales
+        self.n, self.d = base_f32.shape
+        self.rmax = adj.shape[1]
+        self.entry = int(entry)
+        self.dtype = dtype
+        self.handle = roar_index_create(self.n, self.d, _ptr(base_f32), DTYPE_CODES[dtype],
+                                        _ptr(trav), _ptr(scales), _ptr(adj), self.rmax, self.entry,
+                                        max_visits)
+
+    def set_hash_log2(self, log2: int):
+        roar_index_set_hash_log2(self.handle, log2)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            roar_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def search(self, queries, k, L, stream=None, out=None):
+        """Search a CUDA float32 [nq, d] batch; returns (ids int32-bits, dist, visits, hops, status)."""
+        import torch
+
+        assert queries.is_cuda and queries.dtype == torch.float32 and queries.is_contiguous()
+        nq = queries.shape[0]
+        dev = queries.device
+        if out is None:
+            out = (torch.empty((nq, k), dtype=torch.int32, device=dev),
+                   torch.empty((nq, k), dtype=torch.float32, device=dev),
+                   torch.empty(nq, dtype=torch.int32, device=dev),
+                   torch.empty(nq, dtype=torch.int32, device=dev),
+                   torch.empty(nq, dtype=torch.int32, device=dev))
+        ids, dist, visits, hops, status = out
+        roar_search(self.handle, _ptr(queries), nq, k, L, _ptr(ids), _ptr(dist), _ptr(visits),
+                    _ptr(hops), _ptr(status), _stream_ptr(stream))
+        return out
+
+    def search_host(self, queries, k, L, stream=None, out=None):
+        """Host-buffer search (numpy / CPU torch arrays, ideally pinned)."""
+        import torch
+
+        q = queries if isinstance(queries, torch.Tensor) else torch.from_numpy(queries)
+        assert q.dtype == torch.float32 and q.is_contiguous() and not q.is_cuda
+        nq = q.shape[0]
+        if out is None:
+            out = (torch.empty((nq, k), dtype=torch.int32), torch.empty((nq, k), dtype=torch.float32),
+                   torch.empty(nq, dtype=torch.int32), torch.empty(nq, dtype=torch.int32),
+                   torch.empty(nq, dtype=torch.int32))
+        ids, dist, visits, hops, status = out
+        roar_search_host(self.handle, q.data_ptr(), nq, k, L, ids.data_ptr(), dist.data_ptr(),
+                         visits.data_ptr(), hops.data_ptr(), status.data_ptr(), _stream_ptr(stream))
+        return out

@@ -1,0 +1,316 @@
+// C ABI entry points of libroargraph: handle management and search launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "roar_internal.cuh"
+
+namespace roar {
+
+static thread_local char g_last_error[256] = "";
+
+roar_status cuda_fail(cudaError_t e, const char *what) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    return ROAR_ECUDA;
+}
+
+void set_error(const char *msg) { std::snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int next_pow2_log2(uint64_t x) {
+    int lg = 0;
+    while ((1ull << lg) < x) ++lg;
+    return lg;
+}
+
+}  // namespace roar
+
+using namespace roar;
+
+struct roar_index {
+    int64_t n;
+    int32_t d;
+    roar_dtype dtype;
+    const float *base32;
+    const void *trav;
+    const float *scales;
+    const uint32_t *adj;
+    int32_t rmax;
+    uint32_t entry;
+    uint32_t max_visits;
+    int device;
+    int num_sms;
+    int hash_log2_override = 0;
+    // scratch: one overflow visited table per resident warp, grown on demand
+    unsigned long long *spill = nullptr;
+    int64_t spill_slots = 0;
+    int spill_log2 = 0;
+    uint32_t *slot_epoch = nullptr;
+    unsigned int *work = nullptr;
+    // device staging for roar_search_host, grown on demand
+    unsigned char *stage = nullptr;
+    size_t stage_bytes = 0;
+    std::mutex mu;
+};
+
+extern "C" const char *roar_status_string(roar_status s) {
+    switch (s) {
+        case ROAR_OK: return "ok";
+        case ROAR_EINVAL: return "invalid argument";
+        case ROAR_ENOMEM: return "out of memory";
+        case ROAR_ECUDA: return "CUDA error";
+        case ROAR_EOVERFLOW: return "visit cap reached";
+        case ROAR_ETIMEOUT: return "timed out";
+        case ROAR_EBUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *roar_last_error(void) { return g_last_error; }
+
+extern "C" roar_status roar_index_create(int64_t n, int32_t d, const float *base_f32,
+                                         roar_dtype trav_dtype, const void *base_trav,
+                                         const float *scales, const uint32_t *adj, int32_t rmax,
+                                         uint32_t entry, uint32_t max_visits, roar_index **out) {
+    if (!out) return ROAR_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n >= (int64_t)kIdMask || d < 4 || d > 1024 || d % 4 != 0 || !base_f32 || !adj ||
+        rmax < 1 || rmax > ROAR_MAX_RMAX || (int64_t)entry >= n) {
+        set_error("roar_index_create: bad size, pointer or entry");
+        return ROAR_EINVAL;
+    }
+    if (!aligned(base_f32, 16) || !aligned(adj, 4)) {
+        set_error("roar_index_create: base_f32 must be 16-byte and adj 4-byte aligned");
+        return ROAR_EINVAL;
+    }
+    switch (trav_dtype) {
+        case ROAR_F32:
+            if (base_trav || scales) {
+                set_error("roar_index_create: ROAR_F32 takes no copy and no scales");
+                return ROAR_EINVAL;
+            }
+            break;
+        case ROAR_BF16:
+            if (!base_trav || !aligned(base_trav, 8) || scales) {
+                set_error("roar_index_create: ROAR_BF16 needs an 8-byte aligned copy, no scales");
+                return ROAR_EINVAL;
+            }
+            break;
+        case ROAR_FP8_E4M3:
+            if (!base_trav || !aligned(base_trav, 4) || !scales || !aligned(scales, 4)) {
+                set_error("roar_index_create: ROAR_FP8_E4M3 needs a 4-byte aligned copy and scales");
+                return ROAR_EINVAL;
+            }
+            break;
+        default:
+            set_error("roar_index_create: unknown dtype");
+            return ROAR_EINVAL;
+    }
+    if (max_visits == 0) max_visits = 16384u;
+    if (max_visits > (1u << 24)) {
+        set_error("roar_index_create: max_visits above 2^24");
+        return ROAR_EINVAL;
+    }
+    roar_index *idx = new (std::nothrow) roar_index();
+    if (!idx) return ROAR_ENOMEM;
+    idx->n = n;
+    idx->d = d;
+    idx->dtype = trav_dtype;
+    idx->base32 = base_f32;
+    idx->trav = trav_dtype == ROAR_F32 ? (const void *)base_f32 : base_trav;
+    idx->scales = scales;
+    idx->adj = adj;
+    idx->rmax = rmax;
+    idx->entry = entry;
+    idx->max_visits = max_visits;
+    idx->spill_log2 = next_pow2_log2(2ull * ((uint64_t)max_visits + (uint64_t)rmax));
+    cudaError_t e = cudaGetDevice(&idx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&idx->work, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        roar_status st = cuda_fail(e, "roar_index_create");
+        delete idx;
+        return st;
+    }
+    *out = idx;
+    return ROAR_OK;
+}
+
+extern "C" roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2) {
+    if (!idx || (log2 != 0 && (log2 < 5 || log2 > 15))) {
+        set_error("roar_index_set_hash_log2: log2 must be 0 or in [5, 15]");
+        return ROAR_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->mu);
+    idx->hash_log2_override = log2;
+    return ROAR_OK;
+}
+
+extern "C" void roar_index_destroy(roar_index *idx) {
+    if (!idx) return;
+    cudaDeviceSynchronize();
+    cudaFree(idx->spill);
+    cudaFree(idx->slot_epoch);
+    cudaFree(idx->work);
+    cudaFree(idx->stage);
+    delete idx;
+}
+
+namespace roar {
+
+// Make room for `slots` overflow tables (synchronises the device when it grows).
+static roar_status ensure_spill(roar_index *idx, int64_t slots) {
+    if (slots <= idx->spill_slots) return ROAR_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "ensure_spill");
+    cudaFree(idx->spill);
+    cudaFree(idx->slot_epoch);
+    idx->spill = nullptr;
+    idx->slot_epoch = nullptr;
+    idx->spill_slots = 0;
+    const size_t table = (size_t)1 << idx->spill_log2;
+    e = cudaMalloc(&idx->spill, (size_t)slots * table * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&idx->slot_epoch, (size_t)slots * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(idx->spill, 0, (size_t)slots * table * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(idx->slot_epoch, 0, (size_t)slots * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaFree(idx->spill);
+        cudaFree(idx->slot_epoch);
+        idx->spill = nullptr;
+        idx->slot_epoch = nullptr;
+        cudaGetLastError();
+        set_error("roar_search: cannot allocate the overflow visited tables");
+        return ROAR_ENOMEM;
+    }
+    idx->spill_slots = slots;
+    return ROAR_OK;
+}
+
+// Fill a SearchArgs for the handle and pick the launch shape.
+roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &blocks, int64_t nq) {
+    std::memset(&a, 0, sizeof a);
+    a.trav = idx->trav;
+    a.scales = idx->scales;
+    a.base32 = idx->base32;
+    a.adj = idx->adj;
+    a.n = idx->n;
+    a.d = idx->d;
+    a.rmax = idx->rmax;
+    a.entry = idx->entry;
+    a.dtype = (int32_t)idx->dtype;
+    a.lcap = (lmax + 31) / 32 * 32;
+    a.max_visits = idx->max_visits;
+    a.hash_log2 = idx->hash_log2_override ? idx->hash_log2_override : hash_log2_for(lmax);
+    a.spill_log2 = idx->spill_log2;
+    int bps = search_blocks_per_sm((int)idx->dtype, idx->d, a.lcap, a.hash_log2);
+    if (bps <= 0) {
+        set_error("roar_search: this L does not fit in shared memory");
+        return ROAR_EINVAL;
+    }
+    int64_t want = (nq + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    int64_t full = (int64_t)bps * idx->num_sms;
+    blocks = (int)std::max<int64_t>(1, std::min(want, full));
+    roar_status st = ensure_spill(idx, full * kWarpsPerBlock);
+    if (st != ROAR_OK) return st;
+    a.spill = idx->spill;
+    a.slot_epoch = idx->slot_epoch;
+    a.work = idx->work;
+    return ROAR_OK;
+}
+
+}  // namespace roar
+
+extern "C" roar_status roar_search(roar_index *idx, const float *queries, int64_t nq, int32_t k,
+                                   int32_t L, uint32_t *ids, float *dist, uint32_t *visits,
+                                   uint32_t *hops, int32_t *qstatus, void *stream) {
+    if (!idx || nq < 0 || k < 1 || L < k || L > ROAR_MAX_L) {
+        set_error("roar_search: need 1 <= k <= L <= ROAR_MAX_L and nq >= 0");
+        return ROAR_EINVAL;
+    }
+    if (nq == 0) return ROAR_OK;
+    if (nq >= (int64_t)1 << 31 || !queries || !ids || !dist || !aligned(queries, 16)) {
+        set_error("roar_search: bad query or output pointer");
+        return ROAR_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->mu);
+    SearchArgs a;
+    int blocks = 0;
+    roar_status st = plan_search(idx, L, a, blocks, nq);
+    if (st != ROAR_OK) return st;
+    a.q = queries;
+    a.nq = nq;
+    a.k = k;
+    a.L = L;
+    a.ids = ids;
+    a.dist = dist;
+    a.visits = visits;
+    a.hops = hops;
+    a.qstatus = qstatus;
+    cudaError_t e = launch_search(a, blocks, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "roar_search launch");
+    return ROAR_OK;
+}
+
+extern "C" roar_status roar_search_host(roar_index *idx, const float *queries_host, int64_t nq,
+                                        int32_t k, int32_t L, uint32_t *ids_host, float *dist_host,
+                                        uint32_t *visits_host, uint32_t *hops_host,
+                                        int32_t *qstatus_host, void *stream) {
+    if (!idx || nq < 0 || k < 1 || L < k || L > ROAR_MAX_L) {
+        set_error("roar_search_host: need 1 <= k <= L <= ROAR_MAX_L and nq >= 0");
+        return ROAR_EINVAL;
+    }
+    if (nq == 0) return ROAR_OK;
+    if (!queries_host || !ids_host || !dist_host) return ROAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t qb = (size_t)nq * idx->d * sizeof(float);
+    const size_t rb = (size_t)nq * k * sizeof(uint32_t);
+    const size_t sb = (size_t)nq * sizeof(uint32_t);
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t need = up(qb) + 2 * up(rb) + 3 * up(sb);
+    {
+        std::lock_guard<std::mutex> lock(idx->mu);
+        if (need > idx->stage_bytes) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(e, "roar_search_host");
+            cudaFree(idx->stage);
+            idx->stage = nullptr;
+            idx->stage_bytes = 0;
+            e = cudaMalloc(&idx->stage, need);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return ROAR_ENOMEM;
+            }
+            idx->stage_bytes = need;
+        }
+    }
+    unsigned char *p = idx->stage;
+    float *dq = (float *)p;
+    p += up(qb);
+    uint32_t *di = (uint32_t *)p;
+    p += up(rb);
+    float *dd = (float *)p;
+    p += up(rb);
+    uint32_t *dv = (uint32_t *)p;
+    p += up(sb);
+    uint32_t *dh = (uint32_t *)p;
+    p += up(sb);
+    int32_t *ds = (int32_t *)p;
+    cudaError_t e = cudaMemcpyAsync(dq, queries_host, qb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "roar_search_host H2D");
+    roar_status st = roar_search(idx, dq, nq, k, L, di, dd, dv, dh, ds, stream);
+    if (st != ROAR_OK) return st;
+    e = cudaMemcpyAsync(ids_host, di, rb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dist_host, dd, rb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && visits_host) e = cudaMemcpyAsync(visits_host, dv, sb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && hops_host) e = cudaMemcpyAsync(hops_host, dh, sb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && qstatus_host) e = cudaMemcpyAsync(qstatus_host, ds, sb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "roar_search_host D2H");
+    return ROAR_OK;
+}

@@ -1,0 +1,62 @@
+// Internal declarations shared by the CUDA translation units of libroargraph.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "roargraph.h"
+
+namespace roar {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kChecked = 0x80000000u;   // pool entry already expanded
+constexpr uint32_t kIdMask = 0x7FFFFFFFu;
+constexpr int kWarpsPerBlock = 4;            // one query per warp, 4 per CTA
+constexpr int kMaxRowPerLane = ROAR_MAX_RMAX / 32;
+constexpr int kCandCap = ROAR_MAX_RMAX;      // new neighbours per hop, at most rmax
+constexpr int kMaxWarpsPerSm = 32;
+
+// Everything one search launch needs. Plain pointers: the launch reads the
+// index rows, the queries and the scratch, and writes the result arrays.
+struct SearchArgs {
+    const void *trav;        // traversal rows: FP32, BF16 or FP8 [n][d]
+    const float *scales;     // FP8 per-row scales [n] or null
+    const float *base32;     // FP32 rows [n][d] (re-rank)
+    const uint32_t *adj;     // [n][rmax]
+    int64_t n;
+    int32_t d;
+    int32_t rmax;
+    uint32_t entry;
+    int32_t dtype;           // roar_dtype of `trav`
+    const float *q;          // [nq][d]
+    int64_t nq;
+    int32_t k, L;            // uniform k and L ...
+    const int32_t *k_arr;    // ... or per query (uneven batches)
+    const int32_t *L_arr;
+    const int64_t *out_off;  // per-query first result slot (uneven batches)
+    int32_t lcap;            // pool capacity, multiple of 32, >= every L
+    uint32_t max_visits;
+    int32_t hash_log2;       // shared-memory visited-table slots, log2
+    unsigned long long *spill;  // per-warp-slot overflow tables
+    int32_t spill_log2;
+    uint32_t *slot_epoch;    // per-warp-slot tag of the live overflow entries
+    unsigned int *work;      // next unclaimed query (reset per launch)
+    uint32_t *ids;
+    float *dist;
+    uint32_t *visits;
+    uint32_t *hops;
+    int32_t *qstatus;
+};
+
+// Shared memory of one warp: pool + merge copy (16 B per slot), candidate
+// buffers (16 B per slot), visited table (4 B per slot).
+__host__ __device__ inline size_t search_smem_per_warp(int lcap, int hash_log2) {
+    return (size_t)lcap * 16 + (size_t)kCandCap * 16 + ((size_t)4 << hash_log2);
+}
+// Resident CTAs per SM for this configuration (0 if it cannot launch).
+int search_blocks_per_sm(int dtype, int d, int lcap, int hash_log2);
+cudaError_t launch_search(const SearchArgs &a, int blocks, cudaStream_t s);
+
+int hash_log2_for(int L);
+
+}  // namespace roar
