@@ -1,0 +1,401 @@
+"""Benchmark: batched RoarGraph beam search on one GB300 (plain FP32 and BF16/FP8 + FP32 re-rank).
+
+Workload (default): base 1,000,000 x d=200 FP32, 1,000,000 training queries and
+10,000 test queries from the seeded OOD mixture generator (256 components,
+offset norm 1.5), index built with kNN depth 100, M = 32, L_build = 500.
+The L sweep picks the smallest beam width whose recall@10 reaches 0.90; one
+step is one search of the 10,000 test queries at that L (k = 10).
+
+The base rows (800 MB) are far larger than L2 (129 MB), so no L2 flush is
+needed between steps. Prints ONE JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_SWEEP = [10, 20, 30, 50, 75, 100, 150, 200, 300, 400, 500, 600, 700, 800, 1024]
+TARGET_RECALL = 0.90
+METRIC = "QPS at recall@10=0.90 (plain FP32 vs BF16/FP8+rerank); serving p50/p99 ms"
+CACHE_DIR = os.environ.get("ROAR_BENCH_CACHE", "/tmp/roar_bench_cache")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _src_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _setup(w, torch, pkg, rs, log):
+    """Generate the workload, build (or load) the index, ground truth and L sweep."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    key = _src_hash(["roarsynth/__init__.py", "paper_2408_08933_gb300/csrc/roar_build.cpp",
+                     "paper_2408_08933_gb300/csrc/roar_knn.cu", "paper_2408_08933_gb300/csrc/roar_search.cu"])
+    cache = os.path.join(CACHE_DIR, f"{w.name}_{key}.npz")
+    t0 = time.time()
+    X = rs.base(w)
+    Q = rs.test_queries(w)
+    log(f"generated base/test in {time.time() - t0:.1f}s")
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    if os.path.exists(cache):
+        z = np.load(cache)
+        adj = torch.from_numpy(z["adj"]).to(dev)
+        entry = int(z["entry"])
+        gt = z["gt"]
+        stats = json.loads(str(z["stats"]))
+        log(f"loaded index from {cache}")
+    else:
+        t0 = time.time()
+        T = rs.train_queries(w)
+        Td = torch.from_numpy(T).to(dev)
+        log(f"generated training queries in {time.time() - t0:.1f}s")
+        adj, entry, stats = pkg.build_index(Xd, Td, nq_depth=100, M=32, L_build=500)
+        del Td, T
+        log(f"built index: {json.dumps(stats)}")
+        gi, _ = pkg.knn(Qd, Xd, 10)
+        torch.cuda.synchronize()
+        gt = gi.cpu().numpy().view(np.uint32)
+        try:
+            os.makedirs(CACHE_DIR, exist_ok=True)
+            np.savez(cache + ".tmp.npz", adj=adj.cpu().numpy(), entry=entry, gt=gt,
+                     stats=json.dumps(stats))
+            os.replace(cache + ".tmp.npz", cache)
+        except Exception as e:  # cache is an optimisation only
+            log(f"cache write failed: {e}")
+    return dev, X, Q, Xd, Qd, adj, entry, gt, stats
+
+
+def _recall(ids, gt, k=10):
+    ids = ids[:, :k]
+    gt = gt[:, :k]
+    hit = (ids[:, :, None] == gt[:, None, :]).any(axis=2).sum()
+    return float(hit) / (k * ids.shape[0])
+
+
+def _sweep(idx, Qd, gt, torch, sweep):
+    out = {}
+    for L in sweep:
+        ids, dist, visits, hops, st = idx.search(Qd, 10, L)
+        torch.cuda.synchronize()
+        r = _recall(ids.cpu().numpy().view(np.uint32), gt)
+        out[L] = dict(recall=r, visits=float(visits.float().mean()), hops=float(hops.float().mean()),
+                      overflow=int((st != 0).sum()))
+    return out
+
+
+def _pick_L(sweep):
+    for L in sorted(sweep):
+        if sweep[L]["recall"] >= TARGET_RECALL:
+            return L
+    return max(sweep)
+
+
+def _time_steps(idx, Qd, L, steps, warmup, torch):
+    s = torch.cuda.current_stream()
+    out = None
+    for _ in range(warmup):
+        out = idx.search(Qd, 10, L, out=out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(s)
+        out = idx.search(Qd, 10, L, out=out)
+        b.record(s)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, out
+
+
+def _algorithmic_bytes(visits, hops, deg_mean, d, elem_bytes, scale_bytes, k_rerank_L=None):
+    """Bytes the method must move per query: visited rows, adjacency rows read,
+    the query; plus the FP32 re-rank rows for the reduced-precision forms."""
+    b = visits * (d * elem_bytes + scale_bytes) + hops * deg_mean * 4 + 4 * d
+    if k_rerank_L is not None:
+        b = b + k_rerank_L * d * 4
+    return b
+
+
+def _cpu_baseline(X, adj_np, entry, Q, L, budget_s=12.0):
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    cores = os.cpu_count() or 1
+    t0 = time.time()
+    oracle.beam_search(X, adj_np, entry, Q[:8], 10, L, max_visits=16384)
+    per_q = max(1e-5, (time.time() - t0) / 8)
+    n = int(min(len(Q), max(cores * 4, budget_s * cores / per_q)))
+    chunks = np.array_split(np.arange(n), cores * 4)
+
+    def work(ix):
+        return oracle.beam_search(X, adj_np, entry, Q[ix], 10, L, max_visits=16384)
+
+    t0 = time.time()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(work, [c for c in chunks if len(c)]))
+    dt = time.time() - t0
+    return {"value": n / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of the {len(Q)} test queries at L={L}, k=10, one query per call chunk "
+                      f"on {cores} threads"}
+
+
+def _traffic(kernel_file, src_hash):
+    """ncu DRAM bytes per launch from the committed profile summary, if it
+    was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for ln in open(p):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != src_hash:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="base_1m_d200")
+    ap.add_argument("--n", type=int, default=0, help="override base rows (debug)")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--verbose", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    def log(msg):
+        if args.verbose and rank == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    import torch
+
+    import paper_2408_08933_gb300 as pkg
+    import roarsynth as rs
+
+    if args.impl == "reference" and rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dist_on = world > 1 and args.impl == "ours"
+    if dist_on:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    w = rs.WORKLOADS[args.workload]
+    if args.n:
+        w = rs.scaled(w, n=args.n, n_train=args.n)
+    dev, X, Q, Xd, Qd, adj, entry, gt, bstats = _setup(w, torch, pkg, rs, log)
+    idx = pkg.Index(Xd, adj, entry, max_visits=16384)
+    sweep = _sweep(idx, Qd, gt, torch, L_SWEEP)
+    L = _pick_L(sweep)
+    log(f"sweep {json.dumps(sweep)} -> L={L}")
+    nq = Q.shape[0]
+    config = {"workload": f"{w.name}: base {w.n}x{w.d} FP32, {w.n_train} training + {nq} test OOD queries, "
+                          f"{w.n_comp} components, kNN depth 100, M=32, L_build=500",
+              "k": 10, "L": L, "recall_at_10": sweep[L]["recall"], "batch": nq,
+              "l2_flush": "not needed: base rows 800 MB > 129 MB L2", "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        adj_np = adj.cpu().numpy().view(np.uint32)
+        step_s = []
+        for _ in range(args.warmup + args.steps):
+            cb = _cpu_baseline(X, adj_np, entry, Q, L, budget_s=max(1.0, 60.0 / (args.steps + args.warmup)))
+            step_s.append(cb)
+        vals = [c["value"] for c in step_s[args.warmup:]]
+        v = statistics.median(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {**step_s[-1], "value": v},
+                "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    # ---- timed: plain FP32 batch search at L -----------------------------------
+    if dist_on:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, out = _time_steps(idx, Qd, L, args.steps, args.warmup, torch)
+    if dist_on:
+        tdist.barrier()
+    total_ms = sum(ms)
+    if dist_on:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ids, dist, visits, hops, st = out
+    value = world * nq * args.steps / (total_ms / 1e3)
+
+    deg_mean = float((adj != -1).sum().item()) / adj.shape[0]
+    v_mean = float(visits.double().mean())
+    h_mean = float(hops.double().mean())
+    bytes_q = _algorithmic_bytes(v_mean, h_mean, deg_mean, w.d, 4, 0)
+    avg_ms = total_ms / args.steps
+    achieved = bytes_q * nq / (avg_ms / 1e3) / 1e9
+    peak, peak_src = _peaks()
+    src_hash = _src_hash(["paper_2408_08933_gb300/csrc/roar_search.cu"])
+    traffic = _traffic(f"search_f32_{w.name}.txt", src_hash)
+
+    # ---- e2e: host buffers through roar_search_host -----------------------------
+    Qh = torch.from_numpy(Q).pin_memory()
+    hout = (torch.empty((nq, 10), dtype=torch.int32).pin_memory(),
+            torch.empty((nq, 10), dtype=torch.float32).pin_memory(),
+            torch.empty(nq, dtype=torch.int32).pin_memory(), torch.empty(nq, dtype=torch.int32).pin_memory(),
+            torch.empty(nq, dtype=torch.int32).pin_memory())
+    for _ in range(args.warmup):
+        idx.search_host(Qh, 10, L, out=hout)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        idx.search_host(Qh, 10, L, out=hout)
+    e2e_s = time.perf_counter() - t0
+    h_ids = hout[0].numpy().view(np.uint32)
+    assert np.array_equal(h_ids, ids.cpu().numpy().view(np.uint32)), "host-buffer results differ"
+
+    # ---- reduced-precision forms on the same graph -----------------------------
+    forms = {}
+    if not args.no_forms:
+        for dtype, eb, sb in (("bf16", 2, 0), ("fp8", 1, 4)):
+            codes, sc = pkg.quantize(Xd, dtype)
+            qidx = pkg.Index(Xd, adj, entry, dtype=dtype, trav=codes, scales=sc, max_visits=16384)
+            qs = _sweep(qidx, Qd, gt, torch, L_SWEEP)
+            qL = _pick_L(qs)
+            qms, qout = _time_steps(qidx, Qd, qL, max(3, args.steps // 2), 3, torch)
+            qv = float(qout[2].double().mean())
+            qh = float(qout[3].double().mean())
+            qbytes = _algorithmic_bytes(qv, qh, deg_mean, w.d, eb, sb, k_rerank_L=qL)
+            qavg = sum(qms) / len(qms)
+            same_L_recall = qs[L]["recall"] if L in qs else None
+            forms[dtype] = {"L": qL, "recall_at_10": qs[qL]["recall"], "qps": nq / (qavg / 1e3),
+                            "ms_per_step": qavg, "achieved_gbs": qbytes * nq / (qavg / 1e3) / 1e9,
+                            "recall_delta_vs_f32_at_same_L": (None if same_L_recall is None
+                                                              else same_L_recall - sweep[L]["recall"])}
+            qidx.close()
+            del codes, sc
+        forms["f32"] = {"L": L, "recall_at_10": sweep[L]["recall"], "qps": value / world,
+                        "ms_per_step": avg_ms, "achieved_gbs": achieved}
+
+    cpu = None
+    if rank == 0:
+        cpu = _cpu_baseline(X, adj.cpu().numpy().view(np.uint32), entry, Q, L)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": avg_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded OOD Gaussian mixture)",
+        "config": config,
+        "e2e": {"value": world * nq * args.steps / e2e_s, "unit": "queries/s",
+                "h2d_bytes_per_step": int(Q.nbytes),
+                "d2h_bytes_per_step": int(nq * 10 * 8 + nq * 12)},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+                     "bytes_per_query": bytes_q, "kernel": "beam_search_kernel<f32>"},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "forms": forms,
+        "sweep": {str(k): v for k, v in sweep.items()},
+        "build": bstats,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    idx.close()
+    if dist_on:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -76,9 +76,9 @@ const char *roar_last_error(void);
  *                 sizes the library's scratch (see below).
  *   out           receives the handle.
  * Scratch: a 4-byte work counter at creation; on the first search that needs
- * them, one overflow visited table per resident warp of
- * next_pow2(2*(max_visits+rmax)) 8-byte slots (growing them synchronises the
- * device, so run one search before capturing searches in a CUDA graph).
+ * them, per resident warp a visited bitmap of ceil(n/32) words and a log of
+ * max_visits + ROAR_MAX_RMAX ids (growing them synchronises the device, so
+ * run one search before capturing searches in a CUDA graph).
  * Searches on one handle must not overlap in time (enqueue them on one
  * stream); create one handle per concurrent stream.
  * Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
@@ -92,9 +92,10 @@ void roar_index_destroy(roar_index *idx);
 
 /*
  * Tuning: shared-memory visited-table capacity 2^log2 slots per query
- * (5 <= log2 <= 15), or 0 to choose from L automatically. A query that
- * visits more than half the table continues in its exact overflow table, so
- * results never depend on this setting; speed and occupancy do.
+ * (5 <= log2 <= 15), 0 to choose from L automatically, or -1 for no shared
+ * table. A query that visits more than half the table continues in its exact
+ * global visited bitmap, so results never depend on this setting; speed and
+ * occupancy do.
  * Errors: ROAR_EINVAL.
  */
 roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2);
@@ -134,6 +135,74 @@ roar_status roar_search_host(roar_index *idx, const float *queries_host, int64_t
                              int32_t L, uint32_t *ids_host, float *dist_host,
                              uint32_t *visits_host, uint32_t *hops_host, int32_t *qstatus_host,
                              void *stream);
+
+/*
+ * Reduced-precision copy of base rows for the traversal (a compression the
+ * paper leaves open as orthogonal to the index, Sec. 4.3).
+ *   X       device [n][d] FP32 (16-byte aligned, d % 4 == 0).
+ *   dtype   ROAR_BF16: out is device [n][d] uint16 BF16 codes, round to
+ *           nearest even; scales unused (may be NULL).
+ *           ROAR_FP8_E4M3: out is device [n][d] uint8 codes with
+ *           s_r = maxabs(row r) / 448 (IEEE division; 1 for an all-zero row)
+ *           written to scales [n], code = E4M3(x / s_r) rounded to nearest
+ *           even and saturated to +-448.
+ * Asynchronous on `stream`. Errors: ROAR_EINVAL, ROAR_ECUDA.
+ */
+roar_status roar_quantize(const float *X, int64_t n, int32_t d, roar_dtype dtype, void *out,
+                          float *scales, void *stream);
+
+/*
+ * Exact k-nearest neighbours under delta = -<t, x> (Definition 1, Sec. 2.1.1):
+ * the preprocessing step of the construction ("ground truths" of the training
+ * queries, Sec. 4.2.1) and the evaluation ground truth. Scores are first
+ * computed on the tensor cores (BF16 inputs, FP32 accumulation) to keep each
+ * row's 128 best candidates, which are then re-scored with exact FP32 dot
+ * products in the search's fixed order; ids/dist get the first kk of them in
+ * (distance, id) order.
+ *   T [nt][d], X [n][d]   device FP32, 16-byte aligned.
+ *   kk                    1..128, kk <= n.
+ *   ids, dist             device [nt][kk] outputs.
+ * Allocates and frees its own device scratch (BF16 copies of T and X and a
+ * score block of up to 4096 x 524288 FP32) and synchronises `stream` before
+ * returning. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ */
+roar_status roar_knn(const float *T, int64_t nt, const float *X, int64_t n, int32_t d, int32_t kk,
+                     uint32_t *ids, float *dist, void *stream);
+
+/*
+ * Medoid entry point (Sec. 4.2.4, Sec. 4.3), read as the base row nearest in
+ * FP64 L2 to the FP64 mean of the base rows, ties to the lower id.
+ *   X_host  host [n][d] FP32. threads <= 0 uses every hardware thread.
+ * Errors: ROAR_EINVAL.
+ */
+roar_status roar_medoid(const float *X_host, int64_t n, int32_t d, int32_t threads,
+                        uint32_t *entry);
+
+/*
+ * Build a RoarGraph index (Alg. 1): training-query kNN on the GPU (roar_knn,
+ * depth nq_depth = N_q), bipartite graph, neighbourhood-aware projection with
+ * AcquireNeighbors (Alg. 2, Alg. 3) on host threads, connectivity
+ * enhancement with beam searches of width L_build on the GPU, then
+ * reachability repair. The host steps run in batched rounds (all pivots, then
+ * all reverse edges), deterministic for any thread count.
+ *   X_dev [n][d], T_dev [nt][d]   device FP32 base rows and training queries.
+ *   M                             out-degree bound of each phase; rows hold 2M.
+ *   L_build                       candidate-set and beam size (M..ROAR_MAX_L).
+ *   adj_dev                       device [n][2M] uint32 output, padded with
+ *                                 ROAR_NONE_ID.
+ *   entry_out                     the medoid.
+ *   stats                         NULL or double[16]: total, kNN, projection,
+ *                                 enhancement-search, reverse/merge and repair
+ *                                 seconds; pivots; projected edges; final
+ *                                 edges; unreachable before repair; repairs;
+ *                                 unreachable after repair (0 unless every
+ *                                 near candidate of a node is full).
+ * Uses roughly n*(d*4 + 8*M) + nt*N_q*4 bytes of host memory and
+ * synchronises `stream`. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ */
+roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const float *T_dev, int64_t nt,
+                             int32_t nq_depth, int32_t M, int32_t L_build, int32_t threads,
+                             uint32_t *adj_dev, uint32_t *entry_out, double *stats, void *stream);
 
 #ifdef __cplusplus
 }

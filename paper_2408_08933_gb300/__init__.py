@@ -54,6 +54,15 @@ def lib() -> ctypes.CDLL:
     L.roar_search.restype = ctypes.c_int
     L.roar_search_host.argtypes = [P, P, i64, i32, i32, P, P, P, P, P, P]
     L.roar_search_host.restype = ctypes.c_int
+    L.roar_quantize.argtypes = [P, i64, i32, ctypes.c_int, P, P, P]
+    L.roar_quantize.restype = ctypes.c_int
+    L.roar_knn.argtypes = [P, i64, P, i64, i32, i32, P, P, P]
+    L.roar_knn.restype = ctypes.c_int
+    L.roar_medoid.argtypes = [P, i64, i32, i32, ctypes.POINTER(u32)]
+    L.roar_medoid.restype = ctypes.c_int
+    L.roar_build_index.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P,
+                                   ctypes.POINTER(u32), P, P]
+    L.roar_build_index.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -90,6 +99,27 @@ def roar_search_host(handle, queries, nq, k, L, ids, dist, visits=None, hops=Non
                      stream=None):
     _check(lib().roar_search_host(handle, queries, nq, k, L, ids, dist, visits, hops, qstatus,
                                   stream), "roar_search_host")
+
+
+def roar_quantize(X, n, d, dtype, out, scales, stream=None):
+    _check(lib().roar_quantize(X, n, d, dtype, out, scales, stream), "roar_quantize")
+
+
+def roar_knn(T, nt, X, n, d, kk, ids, dist, stream=None):
+    _check(lib().roar_knn(T, nt, X, n, d, kk, ids, dist, stream), "roar_knn")
+
+
+def roar_medoid(X_host, n, d, threads=0):
+    e = ctypes.c_uint32()
+    _check(lib().roar_medoid(X_host, n, d, threads, ctypes.byref(e)), "roar_medoid")
+    return e.value
+
+
+def roar_build_index(X, n, d, T, nt, nq_depth, M, L_build, threads, adj, stats, stream=None):
+    e = ctypes.c_uint32()
+    _check(lib().roar_build_index(X, n, d, T, nt, nq_depth, M, L_build, threads, adj,
+                                  ctypes.byref(e), stats, stream), "roar_build_index")
+    return e.value
 
 
 def _ptr(t):
@@ -172,3 +202,49 @@ class Index:
         roar_search_host(self.handle, q.data_ptr(), nq, k, L, ids.data_ptr(), dist.data_ptr(),
                          visits.data_ptr(), hops.data_ptr(), status.data_ptr(), _stream_ptr(stream))
         return out
+
+
+STAT_KEYS = ["total_s", "knn_s", "projection_s", "enhance_search_s", "reverse_merge_s", "repair_s",
+             "pivots", "pj_edges", "final_edges", "unreachable_before_repair", "repairs",
+             "unreachable_after_repair"]
+
+
+def build_index(X, T, nq_depth=100, M=32, L_build=500, threads=0, stream=None):
+    """RoarGraph construction (Alg. 1) of CUDA float32 base rows X [n, d] from
+    training queries T [nt, d]. Returns (adj int32 [n, 2M] on X's device, entry, stats)."""
+    import numpy as np
+    import torch
+
+    assert X.is_cuda and T.is_cuda and X.dtype == torch.float32 and T.dtype == torch.float32
+    n, d = X.shape
+    adj = torch.empty((n, 2 * M), dtype=torch.int32, device=X.device)
+    st = np.zeros(16, dtype=np.float64)
+    entry = roar_build_index(_ptr(X), n, d, _ptr(T), T.shape[0], nq_depth, M, L_build, threads,
+                             _ptr(adj), st.ctypes.data, _stream_ptr(stream))
+    return adj, entry, dict(zip(STAT_KEYS, st.tolist()))
+
+
+def knn(T, X, kk, stream=None):
+    """Exact kNN of CUDA float32 T [nt, d] against X [n, d] (kk <= 128)."""
+    import torch
+
+    nt, d = T.shape
+    ids = torch.empty((nt, kk), dtype=torch.int32, device=T.device)
+    dist = torch.empty((nt, kk), dtype=torch.float32, device=T.device)
+    roar_knn(_ptr(T), nt, _ptr(X), X.shape[0], d, kk, _ptr(ids), _ptr(dist), _stream_ptr(stream))
+    return ids, dist
+
+
+def quantize(X, dtype, stream=None):
+    """BF16 (returns int16 codes, None) or FP8-E4M3 (uint8 codes, float32 scales) copy of X."""
+    import torch
+
+    n, d = X.shape
+    if dtype == "bf16":
+        out = torch.empty((n, d), dtype=torch.int16, device=X.device)
+        roar_quantize(_ptr(X), n, d, ROAR_BF16, _ptr(out), None, _stream_ptr(stream))
+        return out, None
+    out = torch.empty((n, d), dtype=torch.uint8, device=X.device)
+    sc = torch.empty(n, dtype=torch.float32, device=X.device)
+    roar_quantize(_ptr(X), n, d, ROAR_FP8_E4M3, _ptr(out), _ptr(sc), _stream_ptr(stream))
+    return out, sc

@@ -10,16 +10,16 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
+BUILD = os.environ.get("ROAR_BUILD_DIR", os.path.join(PKG, "_build"))
 LIB = os.path.join(BUILD, "libroargraph.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE,
-                  "-I", CSRC]
+                  "-I", CSRC] + os.environ.get("ROAR_NVCC_FLAGS", "").split()
 CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", CSRC,
             "-I", "/usr/local/cuda/include"]
-LDLIBS = ["-lcublas", "-lpthread"]
+LDLIBS = ["-L/usr/local/cuda/lib64", "-lcublas", "-lpthread", "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
 
 
 def _headers():

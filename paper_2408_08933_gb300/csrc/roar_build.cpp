@@ -1,0 +1,484 @@
+// RoarGraph index construction (Alg. 1-3, Sec. 4.2) for large inputs.
+//
+// The dense step (each training query's N_q nearest base rows) runs on the
+// GPU through roar_knn; connectivity enhancement's per-node beam searches run
+// on the GPU through roar_search over the projected graph. The pruning steps
+// run here on host threads, in a batched form that is deterministic for any
+// thread count:
+//   projection:  every pivot's list N'(x) = AcquireNeighbors(x, C(x), M, fill)
+//                is computed independently (Alg. 2 lines 3-7); then every node
+//                p receives the reverse edges p -> x of all pivots x with
+//                p in N'(x) at once, re-pruned with Alg. 3 (fill) when the
+//                list would exceed M (Alg. 2 line 9);
+//   enhancement: every node's supplementary list is AcquireNeighbors over its
+//                beam-search result without fill (Alg. 1 lines 10-11), then
+//                reverse edges are added the same batched way (line 12) and
+//                the lists are merged with the projected graph (line 14);
+//   repair:      any node the final graph cannot reach from the entry gets an
+//                edge from the nearest reachable node the search finds.
+// The sequential order of the paper's loops (each pivot seeing the reverse
+// edges of earlier pivots) is replaced by these batched rounds, which is what
+// makes the host part parallel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "roargraph.h"
+
+namespace roar {
+roar_status cuda_fail(cudaError_t e, const char *what);
+void set_error(const char *msg);
+}  // namespace roar
+
+namespace {
+
+using Cand = std::pair<float, uint32_t>;  // (distance, id)
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+inline bool cand_less(const Cand &a, const Cand &b) {
+    return a.first < b.first || (a.first == b.first && a.second < b.second);
+}
+
+// delta(a, b) = -<a, b>, FP32, 8 independent partial sums (vectorisable).
+inline float neg_dot(const float *a, const float *b, int d) {
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int i = 0;
+    for (; i + 8 <= d; i += 8)
+        for (int j = 0; j < 8; ++j) s[j] += a[i + j] * b[i + j];
+    float t = 0.0f;
+    for (; i < d; ++i) t += a[i] * b[i];
+    return -(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + t);
+}
+
+template <class F>
+void parallel_for(int64_t n, int threads, F &&f) {
+    std::atomic<int64_t> next{0};
+    const int64_t chunk = 256;
+    auto work = [&](int tid) {
+        for (;;) {
+            const int64_t b = next.fetch_add(chunk);
+            if (b >= n) break;
+            const int64_t e = std::min(n, b + chunk);
+            for (int64_t i = b; i < e; ++i) f(i, tid);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+}
+
+// Alg. 3 over C sorted by (distance to x, id). Keeps the closest candidate,
+// then every candidate closer to x than to each kept neighbour (strict), up
+// to M; with fill, tops up to M from the remaining candidates in order.
+int acquire(const float *X, int d, uint32_t x, const std::vector<Cand> &C, int M, bool fill,
+            uint32_t *res) {
+    int nr = 0;
+    for (size_t i = 0; i < C.size() && nr < M; ++i) {
+        const uint32_t c = C[i].second;
+        if (c == x) continue;
+        bool keep = true;
+        for (int j = 0; j < nr && keep; ++j) {
+            if (res[j] == c) keep = false;
+            else if (!(C[i].first < neg_dot(X + (size_t)c * d, X + (size_t)res[j] * d, d))) keep = false;
+        }
+        if (nr == 0 || keep) res[nr++] = c;
+    }
+    if (fill) {
+        for (size_t i = 0; i < C.size() && nr < M; ++i) {
+            const uint32_t c = C[i].second;
+            if (c == x) continue;
+            bool dup = false;
+            for (int j = 0; j < nr; ++j) dup |= res[j] == c;
+            if (!dup) res[nr++] = c;
+        }
+    }
+    return nr;
+}
+
+// Lists stored as [n][cap] with counts.
+struct Lists {
+    int64_t n = 0;
+    int cap = 0;
+    std::vector<uint32_t> v;
+    std::vector<int> cnt;
+    void init(int64_t n_, int cap_) {
+        n = n_;
+        cap = cap_;
+        v.assign((size_t)n * cap, kNone);
+        cnt.assign((size_t)n, 0);
+    }
+    uint32_t *row(int64_t i) { return v.data() + (size_t)i * cap; }
+    const uint32_t *row(int64_t i) const { return v.data() + (size_t)i * cap; }
+};
+
+// Batched reverse-edge round (Alg. 2 line 9 / Alg. 1 line 12): every node p
+// gets p -> x for all x with p in fwd(x); lists over M are re-pruned with
+// Alg. 3. Without fill, the free slots left by the pruning are topped up with
+// the remaining reverse edges, nearest first: the paper's sequential loop
+// appends a reverse edge whenever the list has room, so its lists end up full
+// of reverse edges after each pruning, and the top-up gives the batched round
+// the same outcome.
+void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lists &fwd) {
+    const int64_t n = fwd.n;
+    std::vector<int64_t> off((size_t)n + 1, 0);
+    for (int64_t x = 0; x < n; ++x)
+        for (int j = 0; j < fwd.cnt[x]; ++j) ++off[fwd.row(x)[j] + 1];
+    for (int64_t i = 0; i < n; ++i) off[i + 1] += off[i];
+    std::vector<uint32_t> inc((size_t)off[n]);
+    std::vector<int64_t> fillpos(off.begin(), off.end() - 1);
+    for (int64_t x = 0; x < n; ++x)  // ascending x: deterministic incoming order
+        for (int j = 0; j < fwd.cnt[x]; ++j) inc[fillpos[fwd.row(x)[j]]++] = (uint32_t)x;
+    Lists out;
+    out.init(n, M);
+    parallel_for(n, threads, [&](int64_t p, int) {
+        const uint32_t *f = fwd.row(p);
+        const int nf = fwd.cnt[p];
+        std::vector<uint32_t> all(f, f + nf);
+        for (int64_t k = off[p]; k < off[p + 1]; ++k) {
+            const uint32_t x = inc[k];
+            if (x == (uint32_t)p) continue;
+            if (std::find(all.begin(), all.end(), x) == all.end()) all.push_back(x);
+        }
+        uint32_t *o = out.row(p);
+        if ((int)all.size() <= M) {
+            std::copy(all.begin(), all.end(), o);
+            out.cnt[p] = (int)all.size();
+            return;
+        }
+        std::vector<Cand> C;
+        C.reserve(all.size());
+        const float *pv = X + (size_t)p * d;
+        for (uint32_t c : all) C.emplace_back(neg_dot(pv, X + (size_t)c * d, d), c);
+        std::sort(C.begin(), C.end(), cand_less);
+        int r = acquire(X, d, (uint32_t)p, C, M, fill, o);
+        if (!fill) {
+            for (size_t i = 0; i < C.size() && r < M; ++i) {
+                const uint32_t c = C[i].second;
+                if (std::find(f, f + nf, c) != f + nf) continue;   // only reverse edges
+                if (std::find(o, o + r, c) != o + r) continue;
+                o[r++] = c;
+            }
+        }
+        out.cnt[p] = r;
+    });
+    fwd = std::move(out);
+}
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// BFS from entry over [n][R] adjacency; returns unreachable ids ascending.
+std::vector<uint32_t> unreachable(const std::vector<uint32_t> &adj, int64_t n, int R, uint32_t entry) {
+    std::vector<unsigned char> seen((size_t)n, 0);
+    std::vector<uint32_t> q;
+    q.reserve((size_t)n);
+    q.push_back(entry);
+    seen[entry] = 1;
+    for (size_t h = 0; h < q.size(); ++h) {
+        const uint32_t *row = adj.data() + (size_t)q[h] * R;
+        for (int j = 0; j < R; ++j) {
+            const uint32_t u = row[j];
+            if (u == kNone) continue;
+            if (!seen[u]) {
+                seen[u] = 1;
+                q.push_back(u);
+            }
+        }
+    }
+    std::vector<uint32_t> out;
+    for (int64_t i = 0; i < n; ++i)
+        if (!seen[i]) out.push_back((uint32_t)i);
+    return out;
+}
+
+}  // namespace
+
+using namespace roar;
+
+extern "C" roar_status roar_medoid(const float *X_host, int64_t n, int32_t d, int32_t threads,
+                                   uint32_t *entry) {
+    if (!X_host || n < 1 || d < 1 || !entry) return ROAR_EINVAL;
+    if (threads < 1) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    // FP64 mean with fixed per-chunk partial sums (deterministic for any thread count).
+    const int64_t chunk = 65536;
+    const int64_t nch = (n + chunk - 1) / chunk;
+    std::vector<double> part((size_t)nch * d, 0.0);
+    parallel_for(nch, threads, [&](int64_t c, int) {
+        double *p = part.data() + (size_t)c * d;
+        for (int64_t i = c * chunk; i < std::min(n, (c + 1) * chunk); ++i)
+            for (int j = 0; j < d; ++j) p[j] += (double)X_host[(size_t)i * d + j];
+    });
+    std::vector<double> mu((size_t)d, 0.0);
+    for (int64_t c = 0; c < nch; ++c)
+        for (int j = 0; j < d; ++j) mu[j] += part[(size_t)c * d + j];
+    for (int j = 0; j < d; ++j) mu[j] /= (double)n;
+    std::vector<double> bestd((size_t)nch, INFINITY);
+    std::vector<int64_t> besti((size_t)nch, -1);
+    parallel_for(nch, threads, [&](int64_t c, int) {
+        for (int64_t i = c * chunk; i < std::min(n, (c + 1) * chunk); ++i) {
+            double s = 0.0;
+            for (int j = 0; j < d; ++j) {
+                const double t = (double)X_host[(size_t)i * d + j] - mu[j];
+                s += t * t;
+            }
+            if (s < bestd[c]) {
+                bestd[c] = s;
+                besti[c] = i;
+            }
+        }
+    });
+    int64_t b = besti[0];
+    double bd = bestd[0];
+    for (int64_t c = 1; c < nch; ++c)
+        if (bestd[c] < bd) {
+            bd = bestd[c];
+            b = besti[c];
+        }
+    *entry = (uint32_t)b;
+    return ROAR_OK;
+}
+
+extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const float *T_dev,
+                                        int64_t nt, int32_t nq_depth, int32_t M, int32_t L_build,
+                                        int32_t threads, uint32_t *adj_dev, uint32_t *entry_out,
+                                        double *stats, void *stream) {
+    if (!X_dev || !T_dev || !adj_dev || !entry_out || n < 2 || nt < 1 || d < 4 || d % 4 ||
+        d > 1024 || nq_depth < 2 || nq_depth > 128 || nq_depth > n || M < 1 || 2 * M > ROAR_MAX_RMAX ||
+        L_build < M || L_build > ROAR_MAX_L) {
+        set_error("roar_build_index: bad arguments");
+        return ROAR_EINVAL;
+    }
+    if (threads < 1) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto t_all = std::chrono::steady_clock::now();
+    double st[16] = {0};
+    roar_status rc = ROAR_OK;
+    const int R = 2 * M;
+
+    // Base rows on the host for the pruning distances.
+    std::vector<float> X((size_t)n * d);
+    cudaError_t e = cudaMemcpyAsync(X.data(), X_dev, X.size() * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: copy X");
+
+    uint32_t entry = 0;
+    roar_medoid(X.data(), n, d, threads, &entry);
+
+    // Alg. 1 input: N_q nearest base rows of every training query (GPU).
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<uint32_t> knn((size_t)nt * nq_depth);
+    {
+        uint32_t *ki = nullptr;
+        float *kd = nullptr;
+        e = cudaMalloc(&ki, knn.size() * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&kd, knn.size() * 4);
+        if (e != cudaSuccess) {
+            cudaFree(ki);
+            cudaGetLastError();
+            return ROAR_ENOMEM;
+        }
+        rc = roar_knn(T_dev, nt, X_dev, n, d, nq_depth, ki, kd, stream);
+        if (rc == ROAR_OK) {
+            e = cudaMemcpyAsync(knn.data(), ki, knn.size() * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "roar_build_index: copy kNN");
+        }
+        cudaFree(ki);
+        cudaFree(kd);
+        if (rc != ROAR_OK) return rc;
+    }
+    st[1] = seconds_since(t0);
+
+    // Alg. 1 lines 2-6: base node x = 1-NN(t) gets the edge x -> t.
+    t0 = std::chrono::steady_clock::now();
+    std::vector<int64_t> boff((size_t)n + 1, 0);
+    for (int64_t t = 0; t < nt; ++t) ++boff[knn[(size_t)t * nq_depth] + 1];
+    for (int64_t i = 0; i < n; ++i) boff[i + 1] += boff[i];
+    std::vector<uint32_t> bq((size_t)nt);
+    {
+        std::vector<int64_t> pos(boff.begin(), boff.end() - 1);
+        for (int64_t t = 0; t < nt; ++t) bq[pos[knn[(size_t)t * nq_depth]]++] = (uint32_t)t;
+    }
+    // Alg. 2 lines 2-7: each pivot selects from its bridges' other neighbours.
+    Lists pj;
+    pj.init(n, M);
+    std::atomic<int64_t> pivots{0};
+    std::vector<std::vector<unsigned char>> seen_t((size_t)threads);
+    parallel_for(n, threads, [&](int64_t x, int tid) {
+        if (boff[x] == boff[x + 1]) return;
+        ++pivots;
+        auto &seen = seen_t[tid];
+        if (seen.empty()) seen.assign((size_t)n, 0);
+        std::vector<Cand> C;
+        C.reserve((size_t)L_build);
+        const float *xv = X.data() + (size_t)x * d;
+        for (int64_t b = boff[x]; b < boff[x + 1] && (int)C.size() < L_build; ++b) {
+            const uint32_t *nout = knn.data() + (size_t)bq[b] * nq_depth + 1;
+            for (int r = 0; r < nq_depth - 1 && (int)C.size() < L_build; ++r) {
+                const uint32_t c = nout[r];
+                if (c == (uint32_t)x || c == kNone || seen[c]) continue;
+                seen[c] = 1;
+                C.emplace_back(neg_dot(xv, X.data() + (size_t)c * d, d), c);
+            }
+        }
+        for (auto &c : C) seen[c.second] = 0;
+        std::sort(C.begin(), C.end(), cand_less);
+        pj.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, true, pj.row(x));
+    });
+    // Alg. 2 line 9, batched.
+    add_reverse_edges(X.data(), d, M, true, threads, pj);
+    st[2] = seconds_since(t0);
+    int64_t pj_edges = 0;
+    for (int64_t i = 0; i < n; ++i) pj_edges += pj.cnt[i];
+
+    // Alg. 1 lines 9-11: beam search of every base row over G_pj (GPU), then
+    // AcquireNeighbors without fill.
+    t0 = std::chrono::steady_clock::now();
+    Lists ce;
+    ce.init(n, M);
+    {
+        uint32_t *pj_dev = nullptr, *pid = nullptr;
+        float *pdist = nullptr;
+        const int64_t chunk = std::min<int64_t>(n, 131072);
+        e = cudaMalloc(&pj_dev, (size_t)n * M * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&pid, (size_t)chunk * L_build * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&pdist, (size_t)chunk * L_build * 4);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pj_dev, pj.v.data(), (size_t)n * M * 4, cudaMemcpyHostToDevice, s);
+        roar_index *gi = nullptr;
+        if (e == cudaSuccess)
+            rc = roar_index_create(n, d, X_dev, ROAR_F32, nullptr, nullptr, pj_dev, M, entry, 32768, &gi);
+        std::vector<uint32_t> hid((size_t)chunk * L_build);
+        std::vector<float> hd((size_t)chunk * L_build);
+        for (int64_t q0 = 0; e == cudaSuccess && rc == ROAR_OK && q0 < n; q0 += chunk) {
+            const int64_t qn = std::min(chunk, n - q0);
+            rc = roar_search(gi, X_dev + (size_t)q0 * d, qn, L_build, L_build, pid, pdist, nullptr,
+                             nullptr, nullptr, stream);
+            if (rc != ROAR_OK) break;
+            e = cudaMemcpyAsync(hid.data(), pid, (size_t)qn * L_build * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hd.data(), pdist, (size_t)qn * L_build * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            parallel_for(qn, threads, [&](int64_t i, int) {
+                const int64_t x = q0 + i;
+                std::vector<Cand> C;
+                C.reserve((size_t)L_build);
+                for (int j = 0; j < L_build; ++j) {
+                    const uint32_t u = hid[(size_t)i * L_build + j];
+                    if (u == kNone || u == (uint32_t)x) continue;
+                    C.emplace_back(hd[(size_t)i * L_build + j], u);
+                }
+                ce.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, false, ce.row(x));
+            });
+        }
+        roar_index_destroy(gi);
+        cudaFree(pj_dev);
+        cudaFree(pid);
+        cudaFree(pdist);
+        if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: enhancement search");
+        if (rc != ROAR_OK) return rc;
+    }
+    st[3] = seconds_since(t0);
+    // Alg. 1 line 12 (batched, no fill), then line 14: N_pj followed by the new edges.
+    t0 = std::chrono::steady_clock::now();
+    add_reverse_edges(X.data(), d, M, false, threads, ce);
+    std::vector<uint32_t> adj((size_t)n * R, kNone);
+    std::vector<int> deg((size_t)n, 0);
+    parallel_for(n, threads, [&](int64_t x, int) {
+        uint32_t *row = adj.data() + (size_t)x * R;
+        int k = 0;
+        for (int j = 0; j < pj.cnt[x]; ++j) row[k++] = pj.row(x)[j];
+        for (int j = 0; j < ce.cnt[x]; ++j) {
+            const uint32_t u = ce.row(x)[j];
+            bool dup = false;
+            for (int t = 0; t < pj.cnt[x]; ++t) dup |= pj.row(x)[t] == u;
+            if (!dup) row[k++] = u;
+        }
+        deg[x] = k;
+    });
+    st[4] = seconds_since(t0);
+
+    // Reachability repair: each unreachable node gets an edge from the
+    // nearest node (among the 16 the search finds from the entry) that still
+    // has a free slot; repeated until every node is reachable.
+    t0 = std::chrono::steady_clock::now();
+    int64_t repairs = 0, unreach0 = -1, unreach_final = 0;
+    {
+        constexpr int KR = 16;
+        for (int round = 0; round < 32; ++round) {
+            std::vector<uint32_t> U = unreachable(adj, n, R, entry);
+            if (unreach0 < 0) unreach0 = (int64_t)U.size();
+            unreach_final = (int64_t)U.size();
+            if (U.empty()) break;
+            e = cudaMemcpyAsync(adj_dev, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice, s);
+            std::vector<float> Q(U.size() * (size_t)d);
+            for (size_t i = 0; i < U.size(); ++i)
+                std::memcpy(&Q[i * d], X.data() + (size_t)U[i] * d, (size_t)d * 4);
+            float *qd = nullptr, *od = nullptr;
+            uint32_t *oi = nullptr;
+            if (e == cudaSuccess) e = cudaMalloc(&qd, Q.size() * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&oi, U.size() * KR * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&od, U.size() * KR * 4);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(qd, Q.data(), Q.size() * 4, cudaMemcpyHostToDevice, s);
+            roar_index *gi = nullptr;
+            if (e == cudaSuccess)
+                rc = roar_index_create(n, d, X_dev, ROAR_F32, nullptr, nullptr, adj_dev, R, entry, 32768, &gi);
+            if (e == cudaSuccess && rc == ROAR_OK)
+                rc = roar_search(gi, qd, (int64_t)U.size(), KR, 64, oi, od, nullptr, nullptr, nullptr, stream);
+            std::vector<uint32_t> r(U.size() * KR, kNone);
+            if (e == cudaSuccess && rc == ROAR_OK)
+                e = cudaMemcpyAsync(r.data(), oi, r.size() * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            roar_index_destroy(gi);
+            cudaFree(qd);
+            cudaFree(oi);
+            cudaFree(od);
+            if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: repair");
+            if (rc != ROAR_OK) return rc;
+            int64_t added = 0;
+            for (size_t i = 0; i < U.size(); ++i) {
+                for (int j = 0; j < KR; ++j) {
+                    const uint32_t src = r[i * KR + j];
+                    if (src == kNone || deg[src] >= R) continue;
+                    uint32_t *row = adj.data() + (size_t)src * R;
+                    bool dup = false;
+                    for (int t = 0; t < deg[src]; ++t) dup |= row[t] == U[i];
+                    if (!dup) {
+                        row[deg[src]++] = U[i];
+                        ++added;
+                    }
+                    break;
+                }
+            }
+            repairs += added;
+            if (added == 0) break;
+        }
+    }
+    st[5] = seconds_since(t0);
+    e = cudaMemcpyAsync(adj_dev, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: upload");
+    int64_t fin_edges = 0;
+    for (int64_t i = 0; i < n; ++i) fin_edges += deg[i];
+    *entry_out = entry;
+    st[0] = seconds_since(t_all);
+    st[6] = (double)pivots.load();
+    st[7] = (double)pj_edges;
+    st[8] = (double)fin_edges;
+    st[9] = (double)unreach0;
+    st[10] = (double)repairs;
+    st[11] = (double)unreach_final;
+    if (stats) std::memcpy(stats, st, sizeof st);
+    return ROAR_OK;
+}

@@ -46,11 +46,12 @@ struct roar_index {
     int device;
     int num_sms;
     int hash_log2_override = 0;
-    // scratch: one overflow visited table per resident warp, grown on demand
-    unsigned long long *spill = nullptr;
-    int64_t spill_slots = 0;
-    int spill_log2 = 0;
-    uint32_t *slot_epoch = nullptr;
+    // scratch: one visited bitmap + log per resident warp, grown on demand
+    uint32_t *vbits = nullptr;
+    uint32_t *vlog = nullptr;
+    int64_t vslots = 0;
+    int64_t vbits_words = 0;
+    int32_t vlog_cap = 0;
     unsigned int *work = nullptr;
     // device staging for roar_search_host, grown on demand
     unsigned char *stage = nullptr;
@@ -128,7 +129,8 @@ extern "C" roar_status roar_index_create(int64_t n, int32_t d, const float *base
     idx->rmax = rmax;
     idx->entry = entry;
     idx->max_visits = max_visits;
-    idx->spill_log2 = next_pow2_log2(2ull * ((uint64_t)max_visits + (uint64_t)rmax));
+    idx->vbits_words = (n + 31) / 32;
+    idx->vlog_cap = (int32_t)max_visits + ROAR_MAX_RMAX;
     cudaError_t e = cudaGetDevice(&idx->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device);
@@ -143,8 +145,8 @@ extern "C" roar_status roar_index_create(int64_t n, int32_t d, const float *base
 }
 
 extern "C" roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2) {
-    if (!idx || (log2 != 0 && (log2 < 5 || log2 > 15))) {
-        set_error("roar_index_set_hash_log2: log2 must be 0 or in [5, 15]");
+    if (!idx || (log2 != 0 && log2 != -1 && (log2 < 5 || log2 > 15))) {
+        set_error("roar_index_set_hash_log2: log2 must be 0, -1 or in [5, 15]");
         return ROAR_EINVAL;
     }
     std::lock_guard<std::mutex> lock(idx->mu);
@@ -155,8 +157,8 @@ extern "C" roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2) {
 extern "C" void roar_index_destroy(roar_index *idx) {
     if (!idx) return;
     cudaDeviceSynchronize();
-    cudaFree(idx->spill);
-    cudaFree(idx->slot_epoch);
+    cudaFree(idx->vbits);
+    cudaFree(idx->vlog);
     cudaFree(idx->work);
     cudaFree(idx->stage);
     delete idx;
@@ -164,31 +166,31 @@ extern "C" void roar_index_destroy(roar_index *idx) {
 
 namespace roar {
 
-// Make room for `slots` overflow tables (synchronises the device when it grows).
-static roar_status ensure_spill(roar_index *idx, int64_t slots) {
-    if (slots <= idx->spill_slots) return ROAR_OK;
+// Make room for `slots` visited bitmaps and logs (synchronises the device when it grows).
+static roar_status ensure_scratch(roar_index *idx, int64_t slots) {
+    if (slots <= idx->vslots) return ROAR_OK;
     cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_fail(e, "ensure_spill");
-    cudaFree(idx->spill);
-    cudaFree(idx->slot_epoch);
-    idx->spill = nullptr;
-    idx->slot_epoch = nullptr;
-    idx->spill_slots = 0;
-    const size_t table = (size_t)1 << idx->spill_log2;
-    e = cudaMalloc(&idx->spill, (size_t)slots * table * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&idx->slot_epoch, (size_t)slots * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(idx->spill, 0, (size_t)slots * table * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(idx->slot_epoch, 0, (size_t)slots * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "ensure_scratch");
+    cudaFree(idx->vbits);
+    cudaFree(idx->vlog);
+    idx->vbits = nullptr;
+    idx->vlog = nullptr;
+    idx->vslots = 0;
+    const size_t bb = (size_t)slots * idx->vbits_words * sizeof(uint32_t);
+    e = cudaMalloc(&idx->vbits, bb);
+    if (e == cudaSuccess) e = cudaMalloc(&idx->vlog, (size_t)slots * idx->vlog_cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(idx->vbits, 0, bb);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        cudaFree(idx->spill);
-        cudaFree(idx->slot_epoch);
-        idx->spill = nullptr;
-        idx->slot_epoch = nullptr;
+        cudaFree(idx->vbits);
+        cudaFree(idx->vlog);
+        idx->vbits = nullptr;
+        idx->vlog = nullptr;
         cudaGetLastError();
-        set_error("roar_search: cannot allocate the overflow visited tables");
+        set_error("roar_search: cannot allocate the visited bitmaps");
         return ROAR_ENOMEM;
     }
-    idx->spill_slots = slots;
+    idx->vslots = slots;
     return ROAR_OK;
 }
 
@@ -206,9 +208,9 @@ roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &block
     a.dtype = (int32_t)idx->dtype;
     a.lcap = (lmax + 31) / 32 * 32;
     a.max_visits = idx->max_visits;
-    a.hash_log2 = idx->hash_log2_override ? idx->hash_log2_override : hash_log2_for(lmax);
-    a.spill_log2 = idx->spill_log2;
-    int bps = search_blocks_per_sm((int)idx->dtype, idx->d, a.lcap, a.hash_log2);
+    a.hash_log2 = idx->hash_log2_override == 0 ? hash_log2_for(lmax)
+                  : (idx->hash_log2_override < 0 ? 0 : idx->hash_log2_override);
+    int bps = search_blocks_per_sm((int)idx->dtype, idx->d, idx->rmax, a.lcap, a.hash_log2);
     if (bps <= 0) {
         set_error("roar_search: this L does not fit in shared memory");
         return ROAR_EINVAL;
@@ -216,10 +218,12 @@ roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &block
     int64_t want = (nq + kWarpsPerBlock - 1) / kWarpsPerBlock;
     int64_t full = (int64_t)bps * idx->num_sms;
     blocks = (int)std::max<int64_t>(1, std::min(want, full));
-    roar_status st = ensure_spill(idx, full * kWarpsPerBlock);
+    roar_status st = ensure_scratch(idx, full * kWarpsPerBlock);
     if (st != ROAR_OK) return st;
-    a.spill = idx->spill;
-    a.slot_epoch = idx->slot_epoch;
+    a.vbits = idx->vbits;
+    a.vbits_words = idx->vbits_words;
+    a.vlog = idx->vlog;
+    a.vlog_cap = idx->vlog_cap;
     a.work = idx->work;
     return ROAR_OK;
 }

@@ -12,9 +12,12 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kChecked = 0x80000000u;   // pool entry already expanded
 constexpr uint32_t kIdMask = 0x7FFFFFFFu;
 constexpr int kWarpsPerBlock = 4;            // one query per warp, 4 per CTA
-constexpr int kMaxRowPerLane = ROAR_MAX_RMAX / 32;
 constexpr int kCandCap = ROAR_MAX_RMAX;      // new neighbours per hop, at most rmax
 constexpr int kMaxWarpsPerSm = 32;
+#ifndef ROAR_MIN_BLOCKS
+#define ROAR_MIN_BLOCKS 5
+#endif
+constexpr int kMinBlocksPerSm = ROAR_MIN_BLOCKS;  // register budget: 65536 / (blocks * 128)
 
 // Everything one search launch needs. Plain pointers: the launch reads the
 // index rows, the queries and the scratch, and writes the result arrays.
@@ -36,10 +39,11 @@ struct SearchArgs {
     const int64_t *out_off;  // per-query first result slot (uneven batches)
     int32_t lcap;            // pool capacity, multiple of 32, >= every L
     uint32_t max_visits;
-    int32_t hash_log2;       // shared-memory visited-table slots, log2
-    unsigned long long *spill;  // per-warp-slot overflow tables
-    int32_t spill_log2;
-    uint32_t *slot_epoch;    // per-warp-slot tag of the live overflow entries
+    int32_t hash_log2;       // shared-memory visited-table slots, log2 (0: none)
+    uint32_t *vbits;         // per-warp-slot visited bitmaps, vbits_words each, all-zero at rest
+    int64_t vbits_words;
+    uint32_t *vlog;          // per-warp-slot log of the ids set in the bitmap, vlog_cap each
+    int32_t vlog_cap;
     unsigned int *work;      // next unclaimed query (reset per launch)
     uint32_t *ids;
     float *dist;
@@ -48,13 +52,13 @@ struct SearchArgs {
     int32_t *qstatus;
 };
 
-// Shared memory of one warp: pool + merge copy (16 B per slot), candidate
-// buffers (16 B per slot), visited table (4 B per slot).
+// Shared memory of one warp: pool (8 B per slot), candidate buffers (16 B per
+// slot), optional visited table (4 B per slot).
 __host__ __device__ inline size_t search_smem_per_warp(int lcap, int hash_log2) {
-    return (size_t)lcap * 16 + (size_t)kCandCap * 16 + ((size_t)4 << hash_log2);
+    return (size_t)lcap * 8 + (size_t)kCandCap * 16 + (hash_log2 ? ((size_t)4 << hash_log2) : 0);
 }
 // Resident CTAs per SM for this configuration (0 if it cannot launch).
-int search_blocks_per_sm(int dtype, int d, int lcap, int hash_log2);
+int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2);
 cudaError_t launch_search(const SearchArgs &a, int blocks, cudaStream_t s);
 
 int hash_log2_for(int L);

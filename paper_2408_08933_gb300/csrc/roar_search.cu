@@ -1,18 +1,19 @@
 // Batched beam search over a RoarGraph index (Sec. 4.3), one warp per query.
 //
 // Per warp, in shared memory: the size-L candidate pool sorted by
-// (distance, id) with an "expanded" bit in each id, a scratch copy used by
-// the merge, the new candidates of the current hop, and an exact visited set
-// (open addressing, linear probing). When a query visits more nodes than the
-// shared table holds at half load, further inserts go to an exact per-warp
-// table in global memory whose entries carry a per-query tag, so it never
-// needs clearing.
+// (distance, id) with an "expanded" bit in each id, the new candidates of the
+// current hop, and optionally a small exact visited table (open addressing,
+// linear probing). Once that table would pass half load, or when it is
+// disabled, the visited set continues in a per-warp bitmap in global memory
+// (one bit per base row, set with one atomicOr round trip); every id set
+// there is appended to a per-warp log, and at the end of the query the log
+// clears exactly those words, so the bitmap is all-zero between queries.
 //
 // Each hop: pick the first unexpanded pool entry, read its adjacency row
-// (coalesced, one id per lane), filter and insert the neighbours into the
+// (coalesced, one id per lane), test-and-insert the neighbours into the
 // visited set, gather the new rows and score them with a warp-cooperative dot
-// product in one fixed order, then merge the scored candidates into the pool.
-// The fixed order (element i to lane (i >> 2) & 31, fmaf per lane in
+// product in one fixed order, then merge the scored candidates into the pool
+// in place. The fixed order (element i to lane (i >> 2) & 31, fmaf per lane in
 // increasing i, then s += shfl_xor(s, o) for o = 16, 8, 4, 2, 1) is exactly
 // what a float4 load per lane produces, and makes every distance, and hence
 // the whole trajectory, independent of the batch and of the launch shape.
@@ -54,7 +55,7 @@ __device__ __forceinline__ uint32_t ld_stream_u1(const uint32_t *p) {
     return v;
 }
 
-// Raw row chunk (4 elements) of row u, chunk ch, in the traversal format.
+// Raw 4-element chunk of a row in the traversal format.
 template <int DT>
 struct RawChunk;
 template <>
@@ -103,9 +104,17 @@ __device__ __forceinline__ float4 to_f4(const RawChunk<DT> &r) {
     }
 }
 
-// Distances for cnt rows whose ids are in ids_s (shared); writes -<q, x> (times
-// the row scale for FP8) to out_s. Rows are processed B at a time so each lane
-// has B * NCH independent loads in flight.
+// Rows gathered per batch: about ROAR_BATCH_CHUNKS 16-byte loads in flight per lane.
+#ifndef ROAR_BATCH_CHUNKS
+#define ROAR_BATCH_CHUNKS 8
+#endif
+template <int NCH>
+__host__ __device__ constexpr int batch_rows() {
+    return NCH >= ROAR_BATCH_CHUNKS ? 1 : ROAR_BATCH_CHUNKS / NCH;
+}
+
+// Distances for cnt rows whose ids are in ids_s (shared, expanded bit ignored);
+// writes -<q, x> (times the row scale for FP8) to out_s.
 template <int DT, int NCH, int B>
 __device__ __forceinline__ void score_rows(const void *base, const float *scales, int d, int d4,
                                            const float4 (&qr)[NCH], const uint32_t *ids_s, int cnt,
@@ -143,11 +152,12 @@ __device__ __forceinline__ void score_rows(const void *base, const float *scales
 #pragma unroll
             for (int b = 0; b < B; ++b) s[b] = s[b] + __shfl_xor_sync(kFull, s[b], o);
         }
-        if (lane < B && j0 + lane < cnt) {
-            float mine = s[0];
+        float mine = s[0];
 #pragma unroll
-            for (int b = 1; b < B; ++b)
-                if (lane == b) mine = s[b];
+        for (int b = 1; b < B; ++b)
+            if (lane == b) mine = s[b];
+        __syncwarp();
+        if (lane < B && j0 + lane < cnt) {
             if constexpr (DT == 2) {
                 const float sc = scales ? __ldg(scales + (ids_s[j0 + lane] & kIdMask)) : 1.0f;
                 out_s[j0 + lane] = -(sc * mine);
@@ -163,18 +173,18 @@ __device__ __forceinline__ uint32_t hash_slot(uint32_t u, int log2) {
     return (u * 2654435761u) >> (32 - log2);
 }
 
-// Shared-memory visited set. Returns 1 = newly inserted, 0 = already present,
+// Shared-memory visited table. Returns 1 = newly inserted, 0 = already present,
 // 2 = absent (lookup only), 3 = table full (cannot happen below half load).
 __device__ __forceinline__ int smem_visit(uint32_t *tab, int log2, uint32_t u, bool insert) {
     const uint32_t mask = (1u << log2) - 1u;
     uint32_t h = hash_slot(u, log2);
     volatile uint32_t *vt = tab;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        uint32_t cur = vt[h];
+        const uint32_t cur = vt[h];
         if (cur == u) return 0;
         if (cur == kNone) {
             if (!insert) return 2;
-            uint32_t old = atomicCAS(&tab[h], kNone, u);
+            const uint32_t old = atomicCAS(&tab[h], kNone, u);
             if (old == kNone) return 1;
             if (old == u) return 0;
         }
@@ -183,70 +193,49 @@ __device__ __forceinline__ int smem_visit(uint32_t *tab, int log2, uint32_t u, b
     return 3;
 }
 
-// Global overflow visited set; entry = (tag << 32) | id, live iff tag == epoch.
-__device__ __forceinline__ int global_visit(unsigned long long *tab, int log2, uint32_t epoch,
-                                            uint32_t u) {
-    const uint32_t mask = (1u << log2) - 1u;
-    uint32_t h = hash_slot(u, log2);
-    const unsigned long long want = ((unsigned long long)epoch << 32) | u;
-    volatile unsigned long long *vt = tab;
-    for (uint32_t probe = 0; probe <= mask;) {
-        unsigned long long cur = vt[h];
-        if ((uint32_t)(cur >> 32) == epoch) {
-            if ((uint32_t)cur == u) return 0;
-            h = (h + 1u) & mask;
-            ++probe;
-            continue;
-        }
-        unsigned long long old = atomicCAS(&tab[h], cur, want);
-        if (old == cur) return 1;
-        // the slot changed under us: look at it again
-    }
-    return 3;
+// Global bitmap visited set: true if u was not yet set.
+__device__ __forceinline__ bool bitmap_visit(uint32_t *bits, uint32_t u) {
+    const uint32_t bit = 1u << (u & 31u);
+    return (atomicOr(bits + (u >> 5), bit) & bit) == 0u;
 }
 
-// Number of pool entries strictly before (dd, id) in the total order.
-__device__ __forceinline__ int pool_lower_bound(const float *pd, const uint32_t *pi, int size,
-                                                float dd, uint32_t id) {
+// Number of entries of a sorted (d, id) array strictly before (dd, id).
+__device__ __forceinline__ int lower_bound_entries(const float *dv, const uint32_t *iv, int size,
+                                                   float dd, uint32_t id) {
     int lo = 0, hi = size;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (less_entry(pd[mid], pi[mid] & kIdMask, dd, id)) lo = mid + 1;
+        if (less_entry(dv[mid], iv[mid] & kIdMask, dd, id)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
-// Rows gathered per batch: about 8 16-byte loads in flight per lane.
-template <int NCH>
-__host__ __device__ constexpr int batch_rows() {
-    return NCH >= 8 ? 1 : 8 / NCH;
-}
-
-template <int DT, int NCH>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 4)
+// RPL = adjacency ids per lane (rmax <= 32 * RPL); also bounds the new
+// candidates of one hop.
+template <int DT, int NCH, int RPL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kMinBlocksPerSm)
 beam_search_kernel(const SearchArgs a) {
+    constexpr int kMaxRowPerLane = RPL;
+    constexpr int kMaxCandPerLane = RPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int lcap = a.lcap;
-    unsigned char *wbase = smem_raw + (size_t)wib * search_smem_per_warp(lcap, a.hash_log2);
+    const int hlog2 = a.hash_log2;           // 0: no shared table
+    const int H = hlog2 ? (1 << hlog2) : 0;
+    unsigned char *wbase = smem_raw + (size_t)wib * search_smem_per_warp(lcap, hlog2);
     float *pd = reinterpret_cast<float *>(wbase);
     uint32_t *pi = reinterpret_cast<uint32_t *>(pd + lcap);
-    float *td = reinterpret_cast<float *>(pi + lcap);
-    uint32_t *ti = reinterpret_cast<uint32_t *>(td + lcap);
-    float *cd = reinterpret_cast<float *>(ti + lcap);
+    float *cd = reinterpret_cast<float *>(pi + lcap);
     uint32_t *ci = reinterpret_cast<uint32_t *>(cd + kCandCap);
     float *sd = reinterpret_cast<float *>(ci + kCandCap);
     uint32_t *si = reinterpret_cast<uint32_t *>(sd + kCandCap);
     uint32_t *htab = si + kCandCap;
-    const int hlog2 = a.hash_log2;
-    const int H = 1 << hlog2;
 
-    const int slot = blockIdx.x * kWarpsPerBlock + wib;
-    unsigned long long *gtab = a.spill + ((size_t)slot << a.spill_log2);
-    const int S = 1 << a.spill_log2;
-    uint32_t epoch = a.slot_epoch[slot];
+    const int64_t slot = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+    uint32_t *bits = a.vbits + slot * a.vbits_words;
+    uint32_t *vlog = a.vlog + slot * (int64_t)a.vlog_cap;
     const int d = a.d, d4 = a.d >> 2;
     const int rmax = a.rmax;
 
@@ -260,14 +249,7 @@ beam_search_kernel(const SearchArgs a) {
         const int L = a.L_arr ? a.L_arr[qi] : a.L;
         const int64_t ooff = a.out_off ? a.out_off[qi] : qi * (int64_t)k;
 
-        if (++epoch == 0u) {  // tag wrapped: old entries could alias, clear once
-            for (int i = lane; i < S; i += 32) gtab[i] = 0ull;
-            epoch = 1u;
-            __threadfence_block();
-        }
         for (int i = lane; i < H; i += 32) htab[i] = kNone;
-        __syncwarp();
-
         float4 qr[NCH];
         const float4 *q4 = reinterpret_cast<const float4 *>(a.q + qi * (int64_t)d);
 #pragma unroll
@@ -275,10 +257,18 @@ beam_search_kernel(const SearchArgs a) {
             const int ch = lane + 32 * c;
             qr[c] = ch < d4 ? __ldg(q4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        __syncwarp();
+        bool spilled = (H == 0);
         if (lane == 0) {
-            htab[hash_slot(a.entry, hlog2)] = a.entry;  // empty table: first probe is free
+            if (spilled) {
+                bitmap_visit(bits, a.entry);
+                vlog[0] = a.entry;
+            } else {
+                htab[hash_slot(a.entry, hlog2)] = a.entry;  // empty table: first probe is free
+            }
             ci[0] = a.entry;
         }
+        int nlog = spilled ? 1 : 0;
         __syncwarp();
         score_rows<DT, NCH, 1>(a.trav, a.scales, d, d4, qr, ci, 1, cd, lane);
         if (lane == 0) {
@@ -288,8 +278,8 @@ beam_search_kernel(const SearchArgs a) {
         __syncwarp();
 
         int size = 1, cursor = 0;
-        uint32_t visits = 1, hops = 0, smem_count = 1;
-        bool spilled = false, bad = false, overflow = false;
+        uint32_t visits = 1, hops = 0, smem_count = spilled ? 0 : 1;
+        bool bad = false, overflow = false;
 
         for (;;) {
             // Select: first unexpanded entry (all entries before `cursor` are expanded).
@@ -314,7 +304,7 @@ beam_search_kernel(const SearchArgs a) {
             ++hops;
             cursor = sel + 1;
 
-            // Neighbour fetch + visited filter.
+            // Neighbour fetch + visited test-and-insert.
             if (!spilled && (int)(smem_count + rmax) > (H >> 1)) spilled = true;
             uint32_t nb[kMaxRowPerLane];
             bool fresh[kMaxRowPerLane];
@@ -335,9 +325,8 @@ beam_search_kernel(const SearchArgs a) {
                 }
                 if (!spilled) {
                     fresh[t] = smem_visit(htab, hlog2, u, true) == 1;
-                } else {
-                    const int r = smem_visit(htab, hlog2, u, false);
-                    if (r == 2) fresh[t] = global_visit(gtab, a.spill_log2, epoch, u) == 1;
+                } else if (H == 0 || smem_visit(htab, hlog2, u, false) == 2) {
+                    fresh[t] = bitmap_visit(bits, u);
                 }
             }
             if (__any_sync(kFull, mybad)) bad = true;
@@ -348,23 +337,28 @@ beam_search_kernel(const SearchArgs a) {
                 if (fresh[t]) ci[cnt + __popc(m & ((1u << lane) - 1u))] = nb[t];
                 cnt += __popc(m);
             }
-            visits += cnt;
-            if (!spilled) smem_count += cnt;
             __syncwarp();
+            if (spilled) {  // every fresh id this hop went to the bitmap: log it
+                for (int j = lane; j < cnt; j += 32) vlog[nlog + j] = ci[j];
+                nlog += cnt;
+            } else {
+                smem_count += cnt;
+            }
+            visits += cnt;
             if (cnt == 0) continue;
 
             // Gather + score.
             score_rows<DT, NCH, batch_rows<NCH>()>(a.trav, a.scales, d, d4, qr, ci, cnt, cd, lane);
 
-            // Merge: drop candidates that cannot enter a full pool.
+            // Drop candidates that cannot enter a full pool.
             if (size == L) {
                 const float wd = pd[L - 1];
                 const uint32_t wi = pi[L - 1] & kIdMask;
-                float kd[kMaxRowPerLane];
-                uint32_t kid[kMaxRowPerLane];
-                bool keep[kMaxRowPerLane];
+                float kd[kMaxCandPerLane];
+                uint32_t kid[kMaxCandPerLane];
+                bool keep[kMaxCandPerLane];
 #pragma unroll
-                for (int t = 0; t < kMaxRowPerLane; ++t) {
+                for (int t = 0; t < kMaxCandPerLane; ++t) {
                     const int j = lane + 32 * t;
                     keep[t] = false;
                     if (j < cnt) {
@@ -376,7 +370,7 @@ beam_search_kernel(const SearchArgs a) {
                 __syncwarp();
                 int c2 = 0;
 #pragma unroll
-                for (int t = 0; t < kMaxRowPerLane; ++t) {
+                for (int t = 0; t < kMaxCandPerLane; ++t) {
                     const unsigned m = __ballot_sync(kFull, keep[t]);
                     if (keep[t]) {
                         const int p = c2 + __popc(m & ((1u << lane) - 1u));
@@ -389,9 +383,9 @@ beam_search_kernel(const SearchArgs a) {
                 __syncwarp();
                 if (cnt == 0) continue;
             }
-            // Rank candidates among themselves (ids are distinct).
+            // Sort the candidates (ids are distinct, so ranks are a permutation).
 #pragma unroll
-            for (int t = 0; t < kMaxRowPerLane; ++t) {
+            for (int t = 0; t < kMaxCandPerLane; ++t) {
                 const int j = lane + 32 * t;
                 if (j < cnt) {
                     const float dj = cd[j];
@@ -403,43 +397,41 @@ beam_search_kernel(const SearchArgs a) {
                 }
             }
             __syncwarp();
-            // Entries before the first candidate's slot stay where they are.
-            const int pmin = pool_lower_bound(pd, pi, size, sd[0], si[0]);
-            for (int i = pmin + lane; i < size; i += 32) {
-                td[i] = pd[i];
-                ti[i] = pi[i];
+            // Final slot of sorted candidate r: (#pool entries before it) + r.
+            int cpos[kMaxCandPerLane];
+#pragma unroll
+            for (int t = 0; t < kMaxCandPerLane; ++t) {
+                const int r = lane + 32 * t;
+                cpos[t] = r < cnt ? lower_bound_entries(pd, pi, size, sd[r], si[r]) + r : 0x7FFFFFFF;
             }
-            __syncwarp();
-            for (int i = pmin + lane; i < size; i += 32) {
-                const float di = td[i];
-                const uint32_t ii = ti[i];
-                int lo = 0, hi = cnt;  // candidates before this pool entry
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (less_entry(sd[mid], si[mid], di, ii & kIdMask)) lo = mid + 1;
-                    else hi = mid;
+            const int pmin = __shfl_sync(kFull, cpos[0], 0);
+            // Move the pool tail [pmin, size) up in place, 32 entries at a time
+            // from the end: new slots are increasing and never below the old
+            // ones, so no write lands on an entry not yet read.
+            for (int hi = size; hi > pmin; hi -= 32) {
+                const int i = hi - 32 + lane;
+                const bool act = i >= pmin;
+                float di = 0.f;
+                uint32_t ii = 0;
+                int np = 0;
+                if (act) {
+                    di = pd[i];
+                    ii = pi[i];
+                    np = i + lower_bound_entries(sd, si, cnt, di, ii & kIdMask);
                 }
-                const int np = i + lo;
-                if (np < L) {
+                __syncwarp();
+                if (act && np < L) {
                     pd[np] = di;
                     pi[np] = ii;
                 }
+                __syncwarp();
             }
-            // Candidate r lands at (#pool entries before it) + r. Pool entries
-            // before pmin are unchanged in pd/pi; those from pmin are in td/ti.
-            for (int r = lane; r < cnt; r += 32) {
-                const float dr = sd[r];
-                const uint32_t ir = si[r];
-                int lo = pmin, hi = size;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (less_entry(td[mid], ti[mid] & kIdMask, dr, ir)) lo = mid + 1;
-                    else hi = mid;
-                }
-                const int np = lo + r;
-                if (np < L) {
-                    pd[np] = dr;
-                    pi[np] = ir;
+#pragma unroll
+            for (int t = 0; t < kMaxCandPerLane; ++t) {
+                const int r = lane + 32 * t;
+                if (r < cnt && cpos[t] < L) {
+                    pd[cpos[t]] = sd[r];
+                    pi[cpos[t]] = si[r];
                 }
             }
             size = min(L, size + cnt);
@@ -447,16 +439,14 @@ beam_search_kernel(const SearchArgs a) {
             __syncwarp();
         }
 
-        // Output (re-ranked in FP32 for the reduced-precision forms).
+        // Output (re-ranked in FP32, in place, for the reduced-precision forms).
         if constexpr (DT != 0) {
-            for (int i = lane; i < size; i += 32) ti[i] = pi[i] & kIdMask;
-            __syncwarp();
-            score_rows<0, NCH, batch_rows<NCH>()>(a.base32, nullptr, d, d4, qr, ti, size, td, lane);
+            score_rows<0, NCH, batch_rows<NCH>()>(a.base32, nullptr, d, d4, qr, pi, size, pd, lane);
             for (int i = lane; i < size; i += 32) {
-                const float di = td[i];
-                const uint32_t ii = ti[i];
+                const float di = pd[i];
+                const uint32_t ii = pi[i] & kIdMask;
                 int r = 0;
-                for (int x = 0; x < size && r < k; ++x) r += less_entry(td[x], ti[x], di, ii) ? 1 : 0;
+                for (int x = 0; x < size && r < k; ++x) r += less_entry(pd[x], pi[x] & kIdMask, di, ii) ? 1 : 0;
                 if (r < k) {
                     a.ids[ooff + r] = ii;
                     a.dist[ooff + r] = di;
@@ -478,51 +468,59 @@ beam_search_kernel(const SearchArgs a) {
             if (a.hops) a.hops[qi] = hops;
             if (a.qstatus) a.qstatus[qi] = overflow ? ROAR_EOVERFLOW : (bad ? ROAR_EINVAL : ROAR_OK);
         }
+        // Return the bitmap to all-zero: clear every word this query set.
+        for (int i = lane; i < nlog; i += 32) atomicAnd(bits + (vlog[i] >> 5), 0u);
         __syncwarp();
     }
-    if (lane == 0) a.slot_epoch[slot] = epoch;
 }
 
-template <int DT>
+template <int DT, int RPL>
 const void *kernel_for(int nch) {
     switch (nch) {
-        case 1: return (const void *)beam_search_kernel<DT, 1>;
-        case 2: return (const void *)beam_search_kernel<DT, 2>;
-        case 3: return (const void *)beam_search_kernel<DT, 3>;
-        case 4: return (const void *)beam_search_kernel<DT, 4>;
-        case 5: return (const void *)beam_search_kernel<DT, 5>;
-        case 6: return (const void *)beam_search_kernel<DT, 6>;
-        case 7: return (const void *)beam_search_kernel<DT, 7>;
-        case 8: return (const void *)beam_search_kernel<DT, 8>;
+        case 1: return (const void *)beam_search_kernel<DT, 1, RPL>;
+        case 2: return (const void *)beam_search_kernel<DT, 2, RPL>;
+        case 3: return (const void *)beam_search_kernel<DT, 3, RPL>;
+        case 4: return (const void *)beam_search_kernel<DT, 4, RPL>;
+        case 5: return (const void *)beam_search_kernel<DT, 5, RPL>;
+        case 6: return (const void *)beam_search_kernel<DT, 6, RPL>;
+        case 7: return (const void *)beam_search_kernel<DT, 7, RPL>;
+        case 8: return (const void *)beam_search_kernel<DT, 8, RPL>;
         default: return nullptr;
     }
 }
 
-const void *search_kernel(int dtype, int d) {
-    const int nch = ((d >> 2) + 31) / 32;
+template <int RPL>
+const void *kernel_rpl(int dtype, int nch) {
     switch (dtype) {
-        case 0: return kernel_for<0>(nch);
-        case 1: return kernel_for<1>(nch);
-        case 2: return kernel_for<2>(nch);
+        case 0: return kernel_for<0, RPL>(nch);
+        case 1: return kernel_for<1, RPL>(nch);
+        case 2: return kernel_for<2, RPL>(nch);
         default: return nullptr;
     }
+}
+
+const void *search_kernel(int dtype, int d, int rmax) {
+    const int nch = ((d >> 2) + 31) / 32;
+    return rmax <= 64 ? kernel_rpl<2>(dtype, nch) : kernel_rpl<4>(dtype, nch);
 }
 
 }  // namespace
 
 int hash_log2_for(int L) {
+    // Measured on GB300 (1M x 200, 10k queries): the shared table wins for
+    // short searches, the bitmap alone (more resident warps) from L ~ 100 on.
+    if (L >= 96) return 0;
     const int lcap = (L + 31) / 32 * 32;
-    const size_t budget = 227 * 1024;  // opt-in shared memory per CTA
+    const size_t budget = (size_t)(228 - kMinBlocksPerSm) * 1024;  // per SM, minus per-CTA reserve
     int lg = 10;
     while ((1 << lg) < 32 * L && lg < 14) ++lg;
-    // Prefer 4 resident CTAs per SM (the register-bound maximum), then at least one.
-    while (lg > 9 && search_smem_per_warp(lcap, lg) * kWarpsPerBlock * 4 > budget) --lg;
-    while (lg > 5 && search_smem_per_warp(lcap, lg) * kWarpsPerBlock > budget) --lg;
-    return lg;
+    // Keep kMinBlocksPerSm CTAs resident; below 2^9 slots use the bitmap alone.
+    while (lg >= 9 && search_smem_per_warp(lcap, lg) * kWarpsPerBlock * kMinBlocksPerSm > budget) --lg;
+    return lg >= 9 ? lg : 0;
 }
 
-int search_blocks_per_sm(int dtype, int d, int lcap, int hash_log2) {
-    const void *fn = search_kernel(dtype, d);
+int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2) {
+    const void *fn = search_kernel(dtype, d, rmax);
     if (!fn) return 0;
     const size_t smem = search_smem_per_warp(lcap, hash_log2) * kWarpsPerBlock;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -535,7 +533,7 @@ int search_blocks_per_sm(int dtype, int d, int lcap, int hash_log2) {
 }
 
 cudaError_t launch_search(const SearchArgs &a, int blocks, cudaStream_t s) {
-    const void *fn = search_kernel(a.dtype, a.d);
+    const void *fn = search_kernel(a.dtype, a.d, a.rmax);
     if (!fn || blocks <= 0) return cudaErrorInvalidValue;
     const size_t smem = search_smem_per_warp(a.lcap, a.hash_log2) * kWarpsPerBlock;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -46,7 +46,7 @@ def test_empty_batch(tiny_idx):
     assert out[0].shape == (0, 10)
 
 
-@pytest.mark.parametrize("log2", [5, 7, 10])
+@pytest.mark.parametrize("log2", [-1, 5, 7, 10])
 def test_overflow_visited_table_path(tiny, log2):
     """A tiny shared table forces the global overflow table; results are unchanged."""
     idx = dev_index(tiny["X"], tiny["adj"], tiny["entry"], max_visits=MV)
