@@ -164,10 +164,12 @@ def _sweep(idx, Qd, gt, torch, sweep):
 
 
 def _pick_L(sweep):
+    """Smallest L reaching the target recall; if none does, the L with the
+    highest recall (reported with recall_target_reached = false)."""
     for L in sorted(sweep):
         if sweep[L]["recall"] >= TARGET_RECALL:
-            return L
-    return max(sweep)
+            return L, True
+    return max(sweep, key=lambda L: (sweep[L]["recall"], -L)), False
 
 
 def _time_steps(idx, Qd, L, steps, warmup, torch):
@@ -278,12 +280,17 @@ def main():
     dev, X, Q, Xd, Qd, adj, entry, gt, bstats = _setup(w, torch, pkg, rs, log)
     idx = pkg.Index(Xd, adj, entry, max_visits=16384)
     sweep = _sweep(idx, Qd, gt, torch, L_SWEEP)
-    L = _pick_L(sweep)
+    L, reached = _pick_L(sweep)
     log(f"sweep {json.dumps(sweep)} -> L={L}")
+    best, tune_ms = idx.autotune(Qd, 10, L, repeats=2)
+    log(f"autotune L={L}: best variant {best}, ms {[round(float(x), 3) for x in tune_ms]}")
     nq = Q.shape[0]
     config = {"workload": f"{w.name}: base {w.n}x{w.d} FP32, {w.n_train} training + {nq} test OOD queries, "
                           f"{w.n_comp} components, kNN depth 100, M=32, L_build=500",
-              "k": 10, "L": L, "recall_at_10": sweep[L]["recall"], "batch": nq,
+              "k": 10, "L": L, "recall_at_10": sweep[L]["recall"], "recall_target": TARGET_RECALL,
+              "recall_target_reached": reached, "batch": nq,
+              "launch": {"variant": best, "team_warps": [1, 2, 4, 8][best // 4] if best >= 0 else None,
+                         "visited_table": ["auto", "bitmap", "2^10", "2^12"][best % 4] if best >= 0 else None},
               "l2_flush": "not needed: base rows 800 MB > 129 MB L2", "parallelism": f"replicas x{world}"}
 
     if args.impl == "reference":
@@ -308,7 +315,9 @@ def main():
         tdist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed_f32")
         ms, out = _time_steps(idx, Qd, L, args.steps, args.warmup, torch)
+        torch.cuda.nvtx.range_pop()
     if dist_on:
         tdist.barrier()
     total_ms = sum(ms)
@@ -351,7 +360,8 @@ def main():
             codes, sc = pkg.quantize(Xd, dtype)
             qidx = pkg.Index(Xd, adj, entry, dtype=dtype, trav=codes, scales=sc, max_visits=16384)
             qs = _sweep(qidx, Qd, gt, torch, L_SWEEP)
-            qL = _pick_L(qs)
+            qL, _ = _pick_L(qs)
+            qidx.autotune(Qd, 10, qL, repeats=2)
             qms, qout = _time_steps(qidx, Qd, qL, max(3, args.steps // 2), 3, torch)
             qv = float(qout[2].double().mean())
             qh = float(qout[3].double().mean())
@@ -366,6 +376,34 @@ def main():
             del codes, sc
         forms["f32"] = {"L": L, "recall_at_10": sweep[L]["recall"], "qps": value / world,
                         "ms_per_step": avg_ms, "achieved_gbs": achieved}
+
+    # ---- uneven batch: per-query k and L in one graph-captured persistent launch ----
+    uneven = None
+    if not args.no_forms:
+        nu = 65536
+        Qu = rs.test_queries(rs.scaled(w, n_test=nu))
+        ku, Lu = rs.uneven_params(nu, seed_tag=7)
+        Qud = torch.from_numpy(Qu).to(dev)
+        kud, Lud = torch.from_numpy(ku).to(dev), torch.from_numpy(Lu).to(dev)
+        uout = idx.uneven_outputs(ku)
+        idx.autotune(Qud[:8192], 10, int(Lu.max()), repeats=1)   # the launch's pool-size bucket
+        plan = idx.plan_uneven(Qud, kud, Lud, int(Lu.max()), uout, longest_first=True)
+        for _ in range(2):
+            plan.launch()
+        torch.cuda.synchronize()
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record()
+        reps = 3
+        for _ in range(reps):
+            plan.launch()
+        b_ev.record()
+        torch.cuda.synchronize()
+        ums = a_ev.elapsed_time(b_ev) / reps
+        uneven = {"queries": nu, "k": "U{1,10,100}", "L": "U[max(k,10),500]", "ms_per_launch": ums,
+                  "qps": nu / (ums / 1e3), "graph_captured": True, "order": "longest L first",
+                  "mean_visits": float(uout[3].double().mean()), "status_nonzero": int((uout[5] != 0).sum())}
+        plan.close()
+        del Qud, uout
 
     cpu = None
     if rank == 0:
@@ -387,6 +425,7 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "forms": forms,
+        "uneven": uneven,
         "sweep": {str(k): v for k, v in sweep.items()},
         "build": bstats,
     }

@@ -51,6 +51,7 @@ typedef enum {
 #define ROAR_MAX_K ROAR_MAX_L
 
 typedef struct roar_index roar_index;
+typedef struct roar_plan roar_plan;
 
 /* Text for a status code (static storage). */
 const char *roar_status_string(roar_status s);
@@ -135,6 +136,67 @@ roar_status roar_search_host(roar_index *idx, const float *queries_host, int64_t
                              int32_t L, uint32_t *ids_host, float *dist_host,
                              uint32_t *visits_host, uint32_t *hops_host, int32_t *qstatus_host,
                              void *stream);
+
+/*
+ * Uneven batch: roar_search with a per-query k and L (the paper's beam search,
+ * Sec. 4.3, at each query's own beam width), all queries in one persistent
+ * launch whose teams pull queries from a device work counter.
+ *   k_dev, L_dev   device [nq] int32: 1 <= k <= L <= L_max per query; a query
+ *                  outside that range gets qstatus ROAR_EINVAL and no output.
+ *   out_off        device [nq] int64: first result slot of each query in
+ *                  ids/dist (query q writes k[q] slots from out_off[q]).
+ *   L_max          the largest L (sizes the shared-memory pool), <= ROAR_MAX_L.
+ *   order          device [nq] int32 processing order (a permutation), or NULL
+ *                  for 0..nq-1; results are the same in any order.
+ * Other arguments as roar_search. Errors: ROAR_EINVAL, ROAR_ECUDA.
+ */
+roar_status roar_search_uneven(roar_index *idx, const float *queries, int64_t nq,
+                               const int32_t *k_dev, const int32_t *L_dev, const int64_t *out_off,
+                               int32_t L_max, const int32_t *order, uint32_t *ids, float *dist,
+                               uint32_t *visits, uint32_t *hops, int32_t *qstatus, void *stream);
+
+/*
+ * Capture one roar_search_uneven launch (its buffers fixed) into a CUDA graph
+ * for repeated replays with roar_plan_launch. With longest_first != 0 the
+ * queries are processed in decreasing L (reads L_dev once, synchronising
+ * `stream`), which shortens the launch's tail. The plan borrows every buffer
+ * and the handle; the handle's scratch is sized before capture. Searches on
+ * the handle must not overlap a replay. Errors: ROAR_EINVAL, ROAR_ENOMEM,
+ * ROAR_ECUDA.
+ */
+roar_status roar_plan_create(roar_index *idx, const float *queries, int64_t nq, const int32_t *k_dev,
+                             const int32_t *L_dev, const int64_t *out_off, int32_t L_max,
+                             int32_t longest_first, uint32_t *ids, float *dist, uint32_t *visits,
+                             uint32_t *hops, int32_t *qstatus, void *stream, roar_plan **out);
+
+/* Replay a plan on `stream`. Errors: ROAR_EINVAL, ROAR_ECUDA. */
+roar_status roar_plan_launch(roar_plan *plan, void *stream);
+
+/* Release a plan (synchronises the device first). NULL is ignored. */
+void roar_plan_destroy(roar_plan *plan);
+
+/*
+ * Launch tuning for the beam-width bucket that contains L (L <= 32, 64, 128,
+ * 256, 512, 1024): team_warps in {1, 2, 4, 8} warps per query (32..256
+ * threads), hash_log2 as in roar_index_set_hash_log2, blocks_per_sm_cap = 0
+ * for the occupancy limit. Results never depend on the tuning.
+ * Errors: ROAR_EINVAL.
+ */
+roar_status roar_index_set_tuning(roar_index *idx, int32_t L, int32_t team_warps, int32_t hash_log2,
+                                  int32_t blocks_per_sm_cap);
+
+/*
+ * Autotune the bucket of L on a sample batch: times `repeats` searches of
+ * each of 16 variants (team_warps {1,2,4,8} x visited-table mode {auto,
+ * bitmap only, 2^10, 2^12}) and keeps the fastest in the handle.
+ *   results  NULL or float[16] milliseconds per search, variant
+ *            i = 4 * team_index + mode_index (1e30 where it cannot launch).
+ *   best     NULL or the chosen variant index.
+ * Allocates temporary outputs and synchronises `stream`.
+ * Errors: ROAR_EINVAL, ROAR_ECUDA.
+ */
+roar_status roar_autotune(roar_index *idx, const float *queries, int64_t nq, int32_t k, int32_t L,
+                          int32_t repeats, float *results, int32_t *best, void *stream);
 
 /*
  * Reduced-precision copy of base rows for the traversal (a compression the

@@ -54,6 +54,18 @@ def lib() -> ctypes.CDLL:
     L.roar_search.restype = ctypes.c_int
     L.roar_search_host.argtypes = [P, P, i64, i32, i32, P, P, P, P, P, P]
     L.roar_search_host.restype = ctypes.c_int
+    L.roar_search_uneven.argtypes = [P, P, i64, P, P, P, i32, P, P, P, P, P, P, P]
+    L.roar_search_uneven.restype = ctypes.c_int
+    L.roar_plan_create.argtypes = [P, P, i64, P, P, P, i32, i32, P, P, P, P, P, P, ctypes.POINTER(P)]
+    L.roar_plan_create.restype = ctypes.c_int
+    L.roar_plan_launch.argtypes = [P, P]
+    L.roar_plan_launch.restype = ctypes.c_int
+    L.roar_plan_destroy.argtypes = [P]
+    L.roar_plan_destroy.restype = None
+    L.roar_index_set_tuning.argtypes = [P, i32, i32, i32, i32]
+    L.roar_index_set_tuning.restype = ctypes.c_int
+    L.roar_autotune.argtypes = [P, P, i64, i32, i32, i32, P, P, P]
+    L.roar_autotune.restype = ctypes.c_int
     L.roar_quantize.argtypes = [P, i64, i32, ctypes.c_int, P, P, P]
     L.roar_quantize.restype = ctypes.c_int
     L.roar_knn.argtypes = [P, i64, P, i64, i32, i32, P, P, P]
@@ -99,6 +111,39 @@ def roar_search_host(handle, queries, nq, k, L, ids, dist, visits=None, hops=Non
                      stream=None):
     _check(lib().roar_search_host(handle, queries, nq, k, L, ids, dist, visits, hops, qstatus,
                                   stream), "roar_search_host")
+
+
+def roar_search_uneven(handle, queries, nq, k_dev, L_dev, out_off, L_max, order, ids, dist,
+                       visits=None, hops=None, qstatus=None, stream=None):
+    _check(lib().roar_search_uneven(handle, queries, nq, k_dev, L_dev, out_off, L_max, order, ids,
+                                    dist, visits, hops, qstatus, stream), "roar_search_uneven")
+
+
+def roar_plan_create(handle, queries, nq, k_dev, L_dev, out_off, L_max, longest_first, ids, dist,
+                     visits=None, hops=None, qstatus=None, stream=None):
+    p = ctypes.c_void_p()
+    _check(lib().roar_plan_create(handle, queries, nq, k_dev, L_dev, out_off, L_max, longest_first,
+                                  ids, dist, visits, hops, qstatus, stream, ctypes.byref(p)),
+           "roar_plan_create")
+    return p.value
+
+
+def roar_plan_launch(plan, stream=None):
+    _check(lib().roar_plan_launch(plan, stream), "roar_plan_launch")
+
+
+def roar_plan_destroy(plan):
+    lib().roar_plan_destroy(plan)
+
+
+def roar_index_set_tuning(handle, L, team_warps, hash_log2=0, blocks_per_sm_cap=0):
+    _check(lib().roar_index_set_tuning(handle, L, team_warps, hash_log2, blocks_per_sm_cap),
+           "roar_index_set_tuning")
+
+
+def roar_autotune(handle, queries, nq, k, L, repeats, results, best, stream=None):
+    _check(lib().roar_autotune(handle, queries, nq, k, L, repeats, results, best, stream),
+           "roar_autotune")
 
 
 def roar_quantize(X, n, d, dtype, out, scales, stream=None):
@@ -187,6 +232,49 @@ class Index:
                     _ptr(hops), _ptr(status), _stream_ptr(stream))
         return out
 
+    def set_tuning(self, L, team_warps, hash_log2=0, blocks_per_sm_cap=0):
+        roar_index_set_tuning(self.handle, L, team_warps, hash_log2, blocks_per_sm_cap)
+
+    def autotune(self, queries, k, L, repeats=3, stream=None):
+        """Time the 16 launch variants for L's bucket on `queries`; keeps the fastest."""
+        import numpy as np
+
+        res = np.zeros(16, dtype=np.float32)
+        best = ctypes.c_int32(-1)
+        roar_autotune(self.handle, _ptr(queries), queries.shape[0], k, L, repeats, res.ctypes.data,
+                      ctypes.byref(best), _stream_ptr(stream))
+        return best.value, res
+
+    def uneven_outputs(self, k_host):
+        """Output buffers and offsets for per-query k (numpy int32)."""
+        import numpy as np
+        import torch
+
+        dev = self.base_f32.device
+        off = np.zeros(len(k_host), dtype=np.int64)
+        off[1:] = np.cumsum(k_host.astype(np.int64))[:-1]
+        total = int(k_host.astype(np.int64).sum())
+        nq = len(k_host)
+        return (torch.from_numpy(off).to(dev), torch.empty(total, dtype=torch.int32, device=dev),
+                torch.empty(total, dtype=torch.float32, device=dev),
+                torch.empty(nq, dtype=torch.int32, device=dev), torch.empty(nq, dtype=torch.int32, device=dev),
+                torch.empty(nq, dtype=torch.int32, device=dev))
+
+    def search_uneven(self, queries, k_dev, L_dev, L_max, out, order=None, stream=None):
+        off, ids, dist, visits, hops, status = out
+        roar_search_uneven(self.handle, _ptr(queries), queries.shape[0], _ptr(k_dev), _ptr(L_dev),
+                           _ptr(off), L_max, _ptr(order), _ptr(ids), _ptr(dist), _ptr(visits),
+                           _ptr(hops), _ptr(status), _stream_ptr(stream))
+        return out
+
+    def plan_uneven(self, queries, k_dev, L_dev, L_max, out, longest_first=True, stream=None):
+        """Capture one uneven search in a CUDA graph; returns a Plan."""
+        off, ids, dist, visits, hops, status = out
+        h = roar_plan_create(self.handle, _ptr(queries), queries.shape[0], _ptr(k_dev), _ptr(L_dev),
+                             _ptr(off), L_max, 1 if longest_first else 0, _ptr(ids), _ptr(dist),
+                             _ptr(visits), _ptr(hops), _ptr(status), _stream_ptr(stream))
+        return Plan(h, (self, queries, k_dev, L_dev, out))
+
     def search_host(self, queries, k, L, stream=None, out=None):
         """Host-buffer search (numpy / CPU torch arrays, ideally pinned)."""
         import torch
@@ -248,3 +336,24 @@ def quantize(X, dtype, stream=None):
     sc = torch.empty(n, dtype=torch.float32, device=X.device)
     roar_quantize(_ptr(X), n, d, ROAR_FP8_E4M3, _ptr(out), _ptr(sc), _stream_ptr(stream))
     return out, sc
+
+
+class Plan:
+    """A captured uneven search (CUDA graph); keeps its buffers alive."""
+
+    def __init__(self, handle, keep):
+        self.handle, self.keep = handle, keep
+
+    def launch(self, stream=None):
+        roar_plan_launch(self.handle, _stream_ptr(stream))
+
+    def close(self):
+        if self.handle:
+            roar_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

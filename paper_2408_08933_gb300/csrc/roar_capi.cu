@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <numeric>
+#include <vector>
 
 #include "roar_internal.cuh"
 
@@ -45,7 +47,14 @@ struct roar_index {
     uint32_t max_visits;
     int device;
     int num_sms;
-    int hash_log2_override = 0;
+    // Launch tuning per beam-width bucket (L <= 32, 64, ..., 1024):
+    // warps per query team, visited-table mode (0 auto, -1 bitmap only,
+    // 5..15 shared slots log2), resident-CTA cap per SM (0 = occupancy limit).
+    struct Tune {
+        int tw = 1;
+        int hash = 0;
+        int bps_cap = 0;
+    } tune[6];
     // scratch: one visited bitmap + log per resident warp, grown on demand
     uint32_t *vbits = nullptr;
     uint32_t *vlog = nullptr;
@@ -150,7 +159,7 @@ extern "C" roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2) {
         return ROAR_EINVAL;
     }
     std::lock_guard<std::mutex> lock(idx->mu);
-    idx->hash_log2_override = log2;
+    for (auto &t : idx->tune) t.hash = log2;
     return ROAR_OK;
 }
 
@@ -194,9 +203,16 @@ static roar_status ensure_scratch(roar_index *idx, int64_t slots) {
     return ROAR_OK;
 }
 
+int tune_bucket(int L) {
+    int b = 0;
+    while (b < 5 && (32 << b) < L) ++b;
+    return b;
+}
+
 // Fill a SearchArgs for the handle and pick the launch shape.
-roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &blocks, int64_t nq) {
+roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &blocks, int &tw, int64_t nq) {
     std::memset(&a, 0, sizeof a);
+    const roar_index::Tune &t = idx->tune[tune_bucket(lmax)];
     a.trav = idx->trav;
     a.scales = idx->scales;
     a.base32 = idx->base32;
@@ -208,17 +224,19 @@ roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &block
     a.dtype = (int32_t)idx->dtype;
     a.lcap = (lmax + 31) / 32 * 32;
     a.max_visits = idx->max_visits;
-    a.hash_log2 = idx->hash_log2_override == 0 ? hash_log2_for(lmax)
-                  : (idx->hash_log2_override < 0 ? 0 : idx->hash_log2_override);
-    int bps = search_blocks_per_sm((int)idx->dtype, idx->d, idx->rmax, a.lcap, a.hash_log2);
+    a.hash_log2 = t.hash == 0 ? hash_log2_for(lmax) : (t.hash < 0 ? 0 : t.hash);
+    tw = t.tw;
+    int bps = search_blocks_per_sm((int)idx->dtype, idx->d, idx->rmax, a.lcap, a.hash_log2, tw);
     if (bps <= 0) {
         set_error("roar_search: this L does not fit in shared memory");
         return ROAR_EINVAL;
     }
-    int64_t want = (nq + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (t.bps_cap > 0 && bps > t.bps_cap) bps = t.bps_cap;
+    const int tpb = teams_per_block(tw);
+    int64_t want = (nq + tpb - 1) / tpb;
     int64_t full = (int64_t)bps * idx->num_sms;
     blocks = (int)std::max<int64_t>(1, std::min(want, full));
-    roar_status st = ensure_scratch(idx, full * kWarpsPerBlock);
+    roar_status st = ensure_scratch(idx, full * tpb);
     if (st != ROAR_OK) return st;
     a.vbits = idx->vbits;
     a.vbits_words = idx->vbits_words;
@@ -244,8 +262,8 @@ extern "C" roar_status roar_search(roar_index *idx, const float *queries, int64_
     }
     std::lock_guard<std::mutex> lock(idx->mu);
     SearchArgs a;
-    int blocks = 0;
-    roar_status st = plan_search(idx, L, a, blocks, nq);
+    int blocks = 0, tw = 1;
+    roar_status st = plan_search(idx, L, a, blocks, tw, nq);
     if (st != ROAR_OK) return st;
     a.q = queries;
     a.nq = nq;
@@ -256,7 +274,7 @@ extern "C" roar_status roar_search(roar_index *idx, const float *queries, int64_
     a.visits = visits;
     a.hops = hops;
     a.qstatus = qstatus;
-    cudaError_t e = launch_search(a, blocks, (cudaStream_t)stream);
+    cudaError_t e = launch_search(a, blocks, tw, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "roar_search launch");
     return ROAR_OK;
 }
@@ -317,4 +335,226 @@ extern "C" roar_status roar_search_host(roar_index *idx, const float *queries_ho
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "roar_search_host D2H");
     return ROAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batches, CUDA-graph plans and the launch autotuner.
+// ---------------------------------------------------------------------------
+
+namespace roar {
+
+static roar_status fill_uneven(roar_index *idx, const float *queries, int64_t nq, const int32_t *k_dev,
+                               const int32_t *L_dev, const int64_t *out_off, int32_t L_max,
+                               const int32_t *order, uint32_t *ids, float *dist, uint32_t *visits,
+                               uint32_t *hops, int32_t *qstatus, SearchArgs &a, int &blocks, int &tw) {
+    if (!idx || nq < 0 || L_max < 1 || L_max > ROAR_MAX_L) {
+        set_error("roar_search_uneven: need 1 <= L_max <= ROAR_MAX_L and nq >= 0");
+        return ROAR_EINVAL;
+    }
+    if (nq == 0) return ROAR_OK;
+    if (nq >= (int64_t)1 << 31 || !queries || !k_dev || !L_dev || !out_off || !ids || !dist ||
+        !aligned(queries, 16)) {
+        set_error("roar_search_uneven: bad pointer");
+        return ROAR_EINVAL;
+    }
+    roar_status st = plan_search(idx, L_max, a, blocks, tw, nq);
+    if (st != ROAR_OK) return st;
+    a.q = queries;
+    a.nq = nq;
+    a.k_arr = k_dev;
+    a.L_arr = L_dev;
+    a.out_off = out_off;
+    a.order = order;
+    a.ids = ids;
+    a.dist = dist;
+    a.visits = visits;
+    a.hops = hops;
+    a.qstatus = qstatus;
+    return ROAR_OK;
+}
+
+}  // namespace roar
+
+extern "C" roar_status roar_search_uneven(roar_index *idx, const float *queries, int64_t nq,
+                                          const int32_t *k_dev, const int32_t *L_dev,
+                                          const int64_t *out_off, int32_t L_max, const int32_t *order,
+                                          uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops,
+                                          int32_t *qstatus, void *stream) {
+    if (!idx) return ROAR_EINVAL;
+    if (nq == 0) return ROAR_OK;
+    std::lock_guard<std::mutex> lock(idx->mu);
+    SearchArgs a;
+    int blocks = 0, tw = 1;
+    roar_status st = fill_uneven(idx, queries, nq, k_dev, L_dev, out_off, L_max, order, ids, dist,
+                                 visits, hops, qstatus, a, blocks, tw);
+    if (st != ROAR_OK || nq == 0) return st;
+    cudaError_t e = launch_search(a, blocks, tw, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "roar_search_uneven launch");
+    return ROAR_OK;
+}
+
+struct roar_plan {
+    roar_index *idx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t *order = nullptr;  // owned processing order (longest beam first), or null
+};
+
+extern "C" roar_status roar_plan_create(roar_index *idx, const float *queries, int64_t nq,
+                                        const int32_t *k_dev, const int32_t *L_dev,
+                                        const int64_t *out_off, int32_t L_max, int32_t longest_first,
+                                        uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops,
+                                        int32_t *qstatus, void *stream, roar_plan **out) {
+    if (!out || !idx || nq < 1) return ROAR_EINVAL;
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    roar_plan *p = new (std::nothrow) roar_plan();
+    if (!p) return ROAR_ENOMEM;
+    p->idx = idx;
+    cudaError_t e = cudaSuccess;
+    if (longest_first) {
+        // Longest beams first (LPT order) keeps the persistent launch's tail short.
+        std::vector<int32_t> Lh((size_t)nq), ord((size_t)nq);
+        e = cudaMemcpyAsync(Lh.data(), L_dev, (size_t)nq * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) {
+            std::iota(ord.begin(), ord.end(), 0);
+            std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return Lh[x] > Lh[y]; });
+            e = cudaMalloc(&p->order, (size_t)nq * 4);
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(p->order, ord.data(), (size_t)nq * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p->order);
+            delete p;
+            return cuda_fail(e, "roar_plan_create: order");
+        }
+    }
+    std::lock_guard<std::mutex> lock(idx->mu);
+    SearchArgs a;
+    int blocks = 0, tw = 1;
+    roar_status st = fill_uneven(idx, queries, nq, k_dev, L_dev, out_off, L_max, p->order, ids, dist,
+                                 visits, hops, qstatus, a, blocks, tw);
+    if (st == ROAR_OK) {
+        // Capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); replays go to the caller's stream.
+        cudaStream_t cs = nullptr;
+        e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = launch_search(a, blocks, tw, cs, false);
+            e = cudaStreamEndCapture(cs, &p->graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        if (cs) cudaStreamDestroy(cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "roar_plan_create: capture");
+    }
+    if (st != ROAR_OK) {
+        if (p->exec) cudaGraphExecDestroy(p->exec);
+        if (p->graph) cudaGraphDestroy(p->graph);
+        cudaFree(p->order);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return ROAR_OK;
+}
+
+extern "C" roar_status roar_plan_launch(roar_plan *p, void *stream) {
+    if (!p || !p->exec) return ROAR_EINVAL;
+    cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? ROAR_OK : cuda_fail(e, "roar_plan_launch");
+}
+
+extern "C" void roar_plan_destroy(roar_plan *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->order);
+    delete p;
+}
+
+extern "C" roar_status roar_index_set_tuning(roar_index *idx, int32_t L, int32_t team_warps,
+                                             int32_t hash_log2, int32_t blocks_per_sm_cap) {
+    if (!idx || L < 1 || L > ROAR_MAX_L ||
+        !(team_warps == 1 || team_warps == 2 || team_warps == 4 || team_warps == 8) ||
+        (hash_log2 != 0 && hash_log2 != -1 && (hash_log2 < 5 || hash_log2 > 15)) || blocks_per_sm_cap < 0) {
+        set_error("roar_index_set_tuning: bad arguments");
+        return ROAR_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->mu);
+    auto &t = idx->tune[tune_bucket(L)];
+    t.tw = team_warps;
+    t.hash = hash_log2;
+    t.bps_cap = blocks_per_sm_cap;
+    return ROAR_OK;
+}
+
+extern "C" roar_status roar_autotune(roar_index *idx, const float *queries, int64_t nq, int32_t k,
+                                     int32_t L, int32_t repeats, float *results, int32_t *best,
+                                     void *stream) {
+    // Candidate grid: team warps x visited-table mode; results gets
+    // [4 x 4] milliseconds per search (inf where a variant cannot launch).
+    static const int tws[4] = {1, 2, 4, 8};
+    static const int hashes[4] = {0, -1, 10, 12};
+    if (!idx || !queries || nq < 1 || k < 1 || L < k || L > ROAR_MAX_L || repeats < 1) return ROAR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *ids = nullptr;
+    float *dist = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&ids, (size_t)nq * k * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dist, (size_t)nq * k * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaFree(ids);
+        cudaFree(dist);
+        return cuda_fail(e, "roar_autotune");
+    }
+    const int b = tune_bucket(L);
+    const roar_index::Tune saved = idx->tune[b];
+    float best_ms = 1e30f;
+    int best_i = -1;
+    roar_status rc = ROAR_OK;
+    for (int i = 0; i < 16 && rc == ROAR_OK; ++i) {
+        idx->tune[b].tw = tws[i / 4];
+        idx->tune[b].hash = hashes[i % 4];
+        idx->tune[b].bps_cap = 0;
+        float ms = 1e30f;
+        roar_status st = roar_search(idx, queries, nq, k, L, ids, dist, nullptr, nullptr, nullptr, stream);
+        if (st == ROAR_OK) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < repeats && st == ROAR_OK; ++r)
+                st = roar_search(idx, queries, nq, k, L, ids, dist, nullptr, nullptr, nullptr, stream);
+            cudaEventRecord(e1, s);
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) rc = cuda_fail(e, "roar_autotune");
+            else if (st == ROAR_OK) {
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= repeats;
+            }
+        } else if (st != ROAR_EINVAL) {
+            rc = st;
+        }
+        if (results) results[i] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_i = i;
+        }
+    }
+    if (best_i >= 0) {
+        idx->tune[b].tw = tws[best_i / 4];
+        idx->tune[b].hash = hashes[best_i % 4];
+        idx->tune[b].bps_cap = 0;
+    } else {
+        idx->tune[b] = saved;
+    }
+    if (best) *best = best_i;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ids);
+    cudaFree(dist);
+    return rc;
 }

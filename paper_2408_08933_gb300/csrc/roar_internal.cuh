@@ -37,6 +37,7 @@ struct SearchArgs {
     const int32_t *k_arr;    // ... or per query (uneven batches)
     const int32_t *L_arr;
     const int64_t *out_off;  // per-query first result slot (uneven batches)
+    const int32_t *order;    // optional processing order (a permutation of 0..nq-1)
     int32_t lcap;            // pool capacity, multiple of 32, >= every L
     uint32_t max_visits;
     int32_t hash_log2;       // shared-memory visited-table slots, log2 (0: none)
@@ -57,9 +58,18 @@ struct SearchArgs {
 __host__ __device__ inline size_t search_smem_per_warp(int lcap, int hash_log2) {
     return (size_t)lcap * 8 + (size_t)kCandCap * 16 + (hash_log2 ? ((size_t)4 << hash_log2) : 0);
 }
-// Resident CTAs per SM for this configuration (0 if it cannot launch).
-int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2);
-cudaError_t launch_search(const SearchArgs &a, int blocks, cudaStream_t s);
+
+// Per team: the above plus a 16-byte control block (claimed query, hop count, pool size).
+__host__ __device__ inline size_t search_smem_per_team(int lcap, int hash_log2) {
+    return search_smem_per_warp(lcap, hash_log2) + 16;
+}
+// Resident CTAs per SM for this configuration with teams of tw warps (0 if it
+// cannot launch), the teams per CTA, and the launch itself.
+int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, int tw);
+int teams_per_block(int tw);
+cudaError_t launch_search(const SearchArgs &a, int blocks, int tw, cudaStream_t s, bool configure = true);
+template <int DT>
+const void *kernel_table(int nch, int rpl, int tw);
 
 int hash_log2_for(int L);
 

@@ -1,0 +1,552 @@
+#pragma once
+// Batched beam search over a RoarGraph index (Sec. 4.3): the kernel template.
+// Included once per traversal type (roar_search_{f32,bf16,fp8}.cu).
+//
+// Per warp, in shared memory: the size-L candidate pool sorted by
+// (distance, id) with an "expanded" bit in each id, the new candidates of the
+// current hop, and optionally a small exact visited table (open addressing,
+// linear probing). Once that table would pass half load, or when it is
+// disabled, the visited set continues in a per-warp bitmap in global memory
+// (one bit per base row, set with one atomicOr round trip); every id set
+// there is appended to a per-warp log, and at the end of the query the log
+// clears exactly those words, so the bitmap is all-zero between queries.
+//
+// Each hop: pick the first unexpanded pool entry, read its adjacency row
+// (coalesced, one id per lane), test-and-insert the neighbours into the
+// visited set, gather the new rows and score them with a warp-cooperative dot
+// product in one fixed order, then merge the scored candidates into the pool
+// in place. The fixed order (element i to lane (i >> 2) & 31, fmaf per lane in
+// increasing i, then s += shfl_xor(s, o) for o = 16, 8, 4, 2, 1) is exactly
+// what a float4 load per lane produces, and makes every distance, and hence
+// the whole trajectory, independent of the batch and of the launch shape.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "roar_internal.cuh"
+
+namespace roar {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool less_entry(float da, uint32_t ia, float db, uint32_t ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+__device__ __forceinline__ float4 ld_stream_f4(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2 *p) {
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_stream_u1(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Raw 4-element chunk of a row in the traversal format.
+template <int DT>
+struct RawChunk;
+template <>
+struct RawChunk<0> {
+    float4 v;
+};
+template <>
+struct RawChunk<1> {
+    uint2 v;
+};
+template <>
+struct RawChunk<2> {
+    uint32_t v;
+};
+
+template <int DT>
+__device__ __forceinline__ void load_chunk(RawChunk<DT> &r, const void *base, uint32_t u, int d,
+                                           int ch) {
+    if constexpr (DT == 0) {
+        r.v = ld_stream_f4(reinterpret_cast<const float4 *>(static_cast<const float *>(base) +
+                                                            (size_t)u * d) + ch);
+    } else if constexpr (DT == 1) {
+        r.v = ld_stream_u2(reinterpret_cast<const uint2 *>(static_cast<const uint16_t *>(base) +
+                                                           (size_t)u * d) + ch);
+    } else {
+        r.v = ld_stream_u1(reinterpret_cast<const uint32_t *>(static_cast<const uint8_t *>(base) +
+                                                              (size_t)u * d) + ch);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ float4 to_f4(const RawChunk<DT> &r) {
+    if constexpr (DT == 0) {
+        return r.v;
+    } else if constexpr (DT == 1) {
+        // BF16 -> FP32 is exact: the BF16 bits are the top half of the FP32 bits.
+        return make_float4(__uint_as_float(r.v.x << 16), __uint_as_float(r.v.x & 0xFFFF0000u),
+                           __uint_as_float(r.v.y << 16), __uint_as_float(r.v.y & 0xFFFF0000u));
+    } else {
+        // E4M3 -> FP16 -> FP32, both exact. Byte j of the word is element 4ch + j.
+        __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r.v & 0xFFFFu), __NV_E4M3);
+        __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r.v >> 16), __NV_E4M3);
+        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&lo));
+        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&hi));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// Rows gathered per batch: about ROAR_BATCH_CHUNKS 16-byte loads in flight per lane.
+#ifndef ROAR_BATCH_CHUNKS
+#define ROAR_BATCH_CHUNKS 8
+#endif
+template <int NCH>
+__host__ __device__ constexpr int batch_rows() {
+    return NCH >= ROAR_BATCH_CHUNKS ? 1 : ROAR_BATCH_CHUNKS / NCH;
+}
+
+// Distances for rows ids_s[j] (shared, expanded bit ignored), j = first,
+// first + 1, ... in groups of B, groups `step` apart (one warp's share of a
+// team); writes -<q, x> (times the row scale for FP8) to out_s[j].
+template <int DT, int NCH, int B>
+__device__ __forceinline__ void score_rows(const void *base, const float *scales, int d, int d4,
+                                           const float4 (&qr)[NCH], const uint32_t *ids_s, int cnt,
+                                           float *out_s, int lane, int first = 0, int step = B) {
+    for (int j0 = first; j0 < cnt; j0 += step) {
+        RawChunk<DT> raw[B][NCH];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int j = j0 + b;
+            const uint32_t u = j < cnt ? (ids_s[j] & kIdMask) : 0u;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int ch = lane + 32 * c;
+                if (j < cnt && ch < d4) load_chunk<DT>(raw[b][c], base, u, d, ch);
+            }
+        }
+        float s[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            s[b] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int ch = lane + 32 * c;
+                if (ch < d4) {
+                    const float4 x = to_f4<DT>(raw[b][c]);
+                    s[b] = fmaf(qr[c].x, x.x, s[b]);
+                    s[b] = fmaf(qr[c].y, x.y, s[b]);
+                    s[b] = fmaf(qr[c].z, x.z, s[b]);
+                    s[b] = fmaf(qr[c].w, x.w, s[b]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) s[b] = s[b] + __shfl_xor_sync(kFull, s[b], o);
+        }
+        float mine = s[0];
+#pragma unroll
+        for (int b = 1; b < B; ++b)
+            if (lane == b) mine = s[b];
+        __syncwarp();
+        if (lane < B && j0 + lane < cnt) {
+            if constexpr (DT == 2) {
+                const float sc = scales ? __ldg(scales + (ids_s[j0 + lane] & kIdMask)) : 1.0f;
+                out_s[j0 + lane] = -(sc * mine);
+            } else {
+                out_s[j0 + lane] = -mine;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t u, int log2) {
+    return (u * 2654435761u) >> (32 - log2);
+}
+
+// Shared-memory visited table. Returns 1 = newly inserted, 0 = already present,
+// 2 = absent (lookup only), 3 = table full (cannot happen below half load).
+__device__ __forceinline__ int smem_visit(uint32_t *tab, int log2, uint32_t u, bool insert) {
+    const uint32_t mask = (1u << log2) - 1u;
+    uint32_t h = hash_slot(u, log2);
+    volatile uint32_t *vt = tab;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t cur = vt[h];
+        if (cur == u) return 0;
+        if (cur == kNone) {
+            if (!insert) return 2;
+            const uint32_t old = atomicCAS(&tab[h], kNone, u);
+            if (old == kNone) return 1;
+            if (old == u) return 0;
+        }
+        h = (h + 1u) & mask;
+    }
+    return 3;
+}
+
+// Global bitmap visited set: true if u was not yet set.
+__device__ __forceinline__ bool bitmap_visit(uint32_t *bits, uint32_t u) {
+    const uint32_t bit = 1u << (u & 31u);
+    return (atomicOr(bits + (u >> 5), bit) & bit) == 0u;
+}
+
+// Number of entries of a sorted (d, id) array strictly before (dd, id).
+__device__ __forceinline__ int lower_bound_entries(const float *dv, const uint32_t *iv, int size,
+                                                   float dd, uint32_t id) {
+    int lo = 0, hi = size;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (less_entry(dv[mid], iv[mid] & kIdMask, dd, id)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+
+// Launch shape of a team of TW warps per query: CTAs of max(4, TW) warps.
+template <int TW>
+struct TeamShape {
+    static constexpr int kThreads = 32 * (TW > kWarpsPerBlock ? TW : kWarpsPerBlock);
+    static constexpr int kTeams = kThreads / (32 * TW);
+    static constexpr int kMinBlocks =
+        (kMinBlocksPerSm * 32 * kWarpsPerBlock) / kThreads > 0 ? (kMinBlocksPerSm * 32 * kWarpsPerBlock) / kThreads : 1;
+};
+
+// One query per team of TW warps. The leader warp (warp 0 of the team)
+// selects, reads the adjacency row, updates the visited set and merges; all
+// TW warps score the hop's new rows, each a strided share of whole dot
+// products, so every distance is computed exactly as with one warp.
+// RPL = adjacency ids per lane (rmax <= 32 * RPL), which also bounds the new
+// candidates of one hop.
+template <int DT, int NCH, int RPL, int TW>
+__global__ void __launch_bounds__(TeamShape<TW>::kThreads, TeamShape<TW>::kMinBlocks)
+beam_search_kernel(const SearchArgs a) {
+    constexpr int kMaxRowPerLane = RPL;
+    constexpr int kMaxCandPerLane = RPL;
+    constexpr int TPB = TeamShape<TW>::kTeams;
+    constexpr int B = batch_rows<NCH>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int team = warp / TW;
+    const int wt = warp - team * TW;
+    const bool leader = wt == 0;
+    const int lcap = a.lcap;
+    const int hlog2 = a.hash_log2;           // 0: no shared table
+    const int H = hlog2 ? (1 << hlog2) : 0;
+    unsigned char *tbase = smem_raw + (size_t)team * search_smem_per_team(lcap, hlog2);
+    float *pd = reinterpret_cast<float *>(tbase);
+    uint32_t *pi = reinterpret_cast<uint32_t *>(pd + lcap);
+    float *cd = reinterpret_cast<float *>(pi + lcap);
+    uint32_t *ci = reinterpret_cast<uint32_t *>(cd + kCandCap);
+    float *sd = reinterpret_cast<float *>(ci + kCandCap);
+    uint32_t *si = reinterpret_cast<uint32_t *>(sd + kCandCap);
+    uint32_t *htab = si + kCandCap;
+    volatile int *ctl = reinterpret_cast<volatile int *>(htab + H);  // claim, count, size
+
+    const int64_t slot = (int64_t)blockIdx.x * TPB + team;
+    uint32_t *bits = a.vbits + slot * a.vbits_words;
+    uint32_t *vlog = a.vlog + slot * (int64_t)a.vlog_cap;
+    const int d = a.d, d4 = a.d >> 2;
+    const int rmax = a.rmax;
+
+    auto tsync = [&]() {
+        if constexpr (TW == 1) {
+            __syncwarp();
+        } else {
+            asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(TW * 32) : "memory");
+        }
+    };
+
+    for (;;) {
+        if (leader && lane == 0) ctl[0] = (int)atomicAdd(a.work, 1u);
+        tsync();
+        const int64_t claim = (int64_t)(unsigned)ctl[0];
+        if (claim >= a.nq) break;
+        const int64_t qi = a.order ? (int64_t)a.order[claim] : claim;
+        const int k = a.k_arr ? a.k_arr[qi] : a.k;
+        const int L = a.L_arr ? a.L_arr[qi] : a.L;
+        const int64_t ooff = a.out_off ? a.out_off[qi] : qi * (int64_t)k;
+        if (L < 1 || L > lcap || k < 1 || k > L) {  // a bad per-query (k, L): report, skip
+            if (leader && lane == 0) {
+                if (a.visits) a.visits[qi] = 0;
+                if (a.hops) a.hops[qi] = 0;
+                if (a.qstatus) a.qstatus[qi] = ROAR_EINVAL;
+            }
+            continue;
+        }
+
+        float4 qr[NCH];
+        const float4 *q4 = reinterpret_cast<const float4 *>(a.q + qi * (int64_t)d);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int ch = lane + 32 * c;
+            qr[c] = ch < d4 ? __ldg(q4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // Leader-only search state.
+        int size = 1, cursor = 0, nlog = 0;
+        uint32_t visits = 1, hops = 0, smem_count = 0;
+        bool spilled = (H == 0), bad = false, overflow = false;
+        if (leader) {
+            for (int i = lane; i < H; i += 32) htab[i] = kNone;
+            __syncwarp();
+            if (lane == 0) {
+                if (spilled) {
+                    bitmap_visit(bits, a.entry);
+                    vlog[0] = a.entry;
+                } else {
+                    htab[hash_slot(a.entry, hlog2)] = a.entry;  // empty table: first probe is free
+                }
+                ci[0] = a.entry;
+            }
+            nlog = spilled ? 1 : 0;
+            smem_count = spilled ? 0 : 1;
+            __syncwarp();
+            score_rows<DT, NCH, 1>(a.trav, a.scales, d, d4, qr, ci, 1, cd, lane);
+            if (lane == 0) {
+                pd[0] = cd[0];
+                pi[0] = a.entry;
+            }
+            __syncwarp();
+        }
+
+        for (;;) {
+            int cnt = 0;
+            if (leader) {
+                // Select: first unexpanded entry (all entries before `cursor` are expanded).
+                int sel = -1;
+                for (int b0 = cursor & ~31; b0 < size; b0 += 32) {
+                    const int i = b0 + lane;
+                    const bool open = i < size && !(pi[i] & kChecked);
+                    const unsigned m = __ballot_sync(kFull, open);
+                    if (m) {
+                        sel = b0 + __ffs(m) - 1;
+                        break;
+                    }
+                }
+                if (sel >= 0 && visits >= a.max_visits) overflow = true;
+                if (sel < 0 || overflow) {
+                    cnt = -1;
+                } else {
+                    const uint32_t v = pi[sel] & kIdMask;
+                    __syncwarp();
+                    if (lane == 0) pi[sel] = v | kChecked;
+                    ++hops;
+                    cursor = sel + 1;
+
+                    // Neighbour fetch + visited test-and-insert.
+                    if (!spilled && (int)(smem_count + rmax) > (H >> 1)) spilled = true;
+                    uint32_t nb[kMaxRowPerLane];
+                    bool fresh[kMaxRowPerLane];
+                    bool mybad = false;
+#pragma unroll
+                    for (int t = 0; t < kMaxRowPerLane; ++t) {
+                        const int j = lane + 32 * t;
+                        nb[t] = (j < rmax) ? __ldg(a.adj + (size_t)v * rmax + j) : kNone;
+                    }
+#pragma unroll
+                    for (int t = 0; t < kMaxRowPerLane; ++t) {
+                        fresh[t] = false;
+                        const uint32_t u = nb[t];
+                        if (u == kNone) continue;
+                        if ((int64_t)u >= a.n) {
+                            mybad = true;
+                            continue;
+                        }
+                        if (!spilled) {
+                            fresh[t] = smem_visit(htab, hlog2, u, true) == 1;
+                        } else if (H == 0 || smem_visit(htab, hlog2, u, false) == 2) {
+                            fresh[t] = bitmap_visit(bits, u);
+                        }
+                    }
+                    if (__any_sync(kFull, mybad)) bad = true;
+#pragma unroll
+                    for (int t = 0; t < kMaxRowPerLane; ++t) {
+                        const unsigned m = __ballot_sync(kFull, fresh[t]);
+                        if (fresh[t]) ci[cnt + __popc(m & ((1u << lane) - 1u))] = nb[t];
+                        cnt += __popc(m);
+                    }
+                    __syncwarp();
+                    if (spilled) {  // every fresh id this hop went to the bitmap: log it
+                        for (int j = lane; j < cnt; j += 32) vlog[nlog + j] = ci[j];
+                        nlog += cnt;
+                    } else {
+                        smem_count += cnt;
+                    }
+                    visits += cnt;
+                }
+                if (lane == 0) {
+                    ctl[1] = cnt;
+                    ctl[2] = size;
+                }
+            }
+            tsync();
+            cnt = ctl[1];
+            if (cnt < 0) break;
+            if (cnt == 0) continue;
+
+            // Gather + score: warp wt takes row groups wt, wt + TW, ...
+            score_rows<DT, NCH, B>(a.trav, a.scales, d, d4, qr, ci, cnt, cd, lane, wt * B, TW * B);
+            tsync();
+            if (!leader) continue;
+
+            // Drop candidates that cannot enter a full pool.
+            if (size == L) {
+                const float wd = pd[L - 1];
+                const uint32_t wi = pi[L - 1] & kIdMask;
+                float kd[kMaxCandPerLane];
+                uint32_t kid[kMaxCandPerLane];
+                bool keep[kMaxCandPerLane];
+#pragma unroll
+                for (int t = 0; t < kMaxCandPerLane; ++t) {
+                    const int j = lane + 32 * t;
+                    keep[t] = false;
+                    if (j < cnt) {
+                        kd[t] = cd[j];
+                        kid[t] = ci[j];
+                        keep[t] = less_entry(kd[t], kid[t], wd, wi);
+                    }
+                }
+                __syncwarp();
+                int c2 = 0;
+#pragma unroll
+                for (int t = 0; t < kMaxCandPerLane; ++t) {
+                    const unsigned m = __ballot_sync(kFull, keep[t]);
+                    if (keep[t]) {
+                        const int p = c2 + __popc(m & ((1u << lane) - 1u));
+                        cd[p] = kd[t];
+                        ci[p] = kid[t];
+                    }
+                    c2 += __popc(m);
+                }
+                cnt = c2;
+                __syncwarp();
+                if (cnt == 0) continue;
+            }
+            // Sort the candidates (ids are distinct, so ranks are a permutation).
+#pragma unroll
+            for (int t = 0; t < kMaxCandPerLane; ++t) {
+                const int j = lane + 32 * t;
+                if (j < cnt) {
+                    const float dj = cd[j];
+                    const uint32_t ij = ci[j];
+                    int r = 0;
+                    for (int x = 0; x < cnt; ++x) r += less_entry(cd[x], ci[x], dj, ij) ? 1 : 0;
+                    sd[r] = dj;
+                    si[r] = ij;
+                }
+            }
+            __syncwarp();
+            // Final slot of sorted candidate r: (#pool entries before it) + r.
+            int cpos[kMaxCandPerLane];
+#pragma unroll
+            for (int t = 0; t < kMaxCandPerLane; ++t) {
+                const int r = lane + 32 * t;
+                cpos[t] = r < cnt ? lower_bound_entries(pd, pi, size, sd[r], si[r]) + r : 0x7FFFFFFF;
+            }
+            const int pmin = __shfl_sync(kFull, cpos[0], 0);
+            // Move the pool tail [pmin, size) up in place, 32 entries at a time
+            // from the end: new slots are increasing and never below the old
+            // ones, so no write lands on an entry not yet read.
+            for (int hi = size; hi > pmin; hi -= 32) {
+                const int i = hi - 32 + lane;
+                const bool act = i >= pmin;
+                float di = 0.f;
+                uint32_t ii = 0;
+                int np = 0;
+                if (act) {
+                    di = pd[i];
+                    ii = pi[i];
+                    np = i + lower_bound_entries(sd, si, cnt, di, ii & kIdMask);
+                }
+                __syncwarp();
+                if (act && np < L) {
+                    pd[np] = di;
+                    pi[np] = ii;
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int t = 0; t < kMaxCandPerLane; ++t) {
+                const int r = lane + 32 * t;
+                if (r < cnt && cpos[t] < L) {
+                    pd[cpos[t]] = sd[r];
+                    pi[cpos[t]] = si[r];
+                }
+            }
+            size = min(L, size + cnt);
+            cursor = min(cursor, pmin);
+            __syncwarp();
+        }
+
+        // Output (re-ranked in FP32, in place, for the reduced-precision forms).
+        const int fsize = ctl[2];
+        if constexpr (DT != 0) {
+            score_rows<0, NCH, B>(a.base32, nullptr, d, d4, qr, pi, fsize, pd, lane, wt * B, TW * B);
+            tsync();
+            if (leader) {
+                for (int i = lane; i < fsize; i += 32) {
+                    const float di = pd[i];
+                    const uint32_t ii = pi[i] & kIdMask;
+                    int r = 0;
+                    for (int x = 0; x < fsize && r < k; ++x)
+                        r += less_entry(pd[x], pi[x] & kIdMask, di, ii) ? 1 : 0;
+                    if (r < k) {
+                        a.ids[ooff + r] = ii;
+                        a.dist[ooff + r] = di;
+                    }
+                }
+                for (int r = fsize + lane; r < k; r += 32) {
+                    a.ids[ooff + r] = kNone;
+                    a.dist[ooff + r] = __int_as_float(0x7f800000);
+                }
+            }
+        } else if (leader) {
+            for (int r = lane; r < k; r += 32) {
+                const bool have = r < fsize;
+                a.ids[ooff + r] = have ? (pi[r] & kIdMask) : kNone;
+                a.dist[ooff + r] = have ? pd[r] : __int_as_float(0x7f800000);
+            }
+        }
+        if (leader) {
+            if (lane == 0) {
+                if (a.visits) a.visits[qi] = visits;
+                if (a.hops) a.hops[qi] = hops;
+                if (a.qstatus) a.qstatus[qi] = overflow ? ROAR_EOVERFLOW : (bad ? ROAR_EINVAL : ROAR_OK);
+            }
+            // Return the bitmap to all-zero: clear every word this query set.
+            for (int i = lane; i < nlog; i += 32) atomicAnd(bits + (vlog[i] >> 5), 0u);
+            __syncwarp();
+        }
+    }
+}
+
+}  // namespace
+
+// Kernel for (row chunks per lane, adjacency ids per lane, warps per team).
+template <int DT>
+const void *kernel_table(int nch, int rpl, int tw) {
+#define ROAR_K(N, R, T) \
+    if (nch == N && rpl == R && tw == T) return (const void *)beam_search_kernel<DT, N, R, T>;
+#define ROAR_KT(N, R) ROAR_K(N, R, 1) ROAR_K(N, R, 2) ROAR_K(N, R, 4) ROAR_K(N, R, 8)
+#define ROAR_KN(N) ROAR_KT(N, 2) ROAR_KT(N, 4)
+    ROAR_KN(1) ROAR_KN(2) ROAR_KN(4) ROAR_KN(8)
+#undef ROAR_KN
+#undef ROAR_KT
+#undef ROAR_K
+    return nullptr;
+}
+
+}  // namespace roar
