@@ -199,6 +199,36 @@ roar_status roar_autotune(roar_index *idx, const float *queries, int64_t nq, int
                           int32_t repeats, float *results, int32_t *best, void *stream);
 
 /*
+ * FP32 beam search that allocates nothing (no counterpart in the paper: it
+ * serves callers that must not allocate device memory, such as code that runs
+ * inside another framework's memory pool, which owns all device memory, or a
+ * serving process that may not allocate, or synchronise through cudaMalloc,
+ * once it is running). Same search and results as roar_search on an FP32
+ * handle with the default tuning, but with no handle: the index is passed as
+ * plain pointers (arguments as in roar_index_create and roar_search).
+ * Scratch: one fixed 64 MiB device array inside the library (every GPU that
+ * loads the library holds it until the process exits) holding a work counter
+ * and, per resident warp, a visited bitmap of ceil(n/32) words and a visit
+ * log of max_visits + ROAR_MAX_RMAX ids; the number of warps used is what fits
+ * (fewer than roar_search on large n, so it can be slower). Sizes that do not
+ * fit even 4 warps (4 * 4 * (ceil(n/32) + max_visits + 128) bytes > 64 MiB,
+ * e.g. n above about 120 million at the default max_visits) return
+ * ROAR_EINVAL with an explanation in roar_last_error().
+ * The first call on each device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture. Every call clears the parts that must start at zero,
+ * but all calls share the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results.
+ * Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: ROAR_EINVAL, ROAR_ECUDA.
+ */
+roar_status roar_search_noalloc(int64_t n, int32_t d, const float *base_f32, const uint32_t *adj,
+                                int32_t rmax, uint32_t entry, uint32_t max_visits,
+                                const float *queries, int64_t nq, int32_t k, int32_t L,
+                                uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops,
+                                int32_t *qstatus, void *stream);
+
+/*
  * Reduced-precision copy of base rows for the traversal (a compression the
  * paper leaves open as orthogonal to the index, Sec. 4.3).
  *   X       device [n][d] FP32 (16-byte aligned, d % 4 == 0).

@@ -66,6 +66,9 @@ def lib() -> ctypes.CDLL:
     L.roar_index_set_tuning.restype = ctypes.c_int
     L.roar_autotune.argtypes = [P, P, i64, i32, i32, i32, P, P, P]
     L.roar_autotune.restype = ctypes.c_int
+    L.roar_search_noalloc.argtypes = [i64, i32, P, P, i32, u32, u32, P, i64, i32, i32, P, P, P, P,
+                                      P, P]
+    L.roar_search_noalloc.restype = ctypes.c_int
     L.roar_quantize.argtypes = [P, i64, i32, ctypes.c_int, P, P, P]
     L.roar_quantize.restype = ctypes.c_int
     L.roar_knn.argtypes = [P, i64, P, i64, i32, i32, P, P, P]
@@ -144,6 +147,14 @@ def roar_index_set_tuning(handle, L, team_warps, hash_log2=0, blocks_per_sm_cap=
 def roar_autotune(handle, queries, nq, k, L, repeats, results, best, stream=None):
     _check(lib().roar_autotune(handle, queries, nq, k, L, repeats, results, best, stream),
            "roar_autotune")
+
+
+def roar_search_noalloc(n, d, base_f32, adj, rmax, entry, max_visits, queries, nq, k, L, ids, dist,
+                        visits=None, hops=None, qstatus=None, stream=None):
+    """Raw C-ABI call of the search that allocates nothing (pointer arguments are integers)."""
+    _check(lib().roar_search_noalloc(n, d, base_f32, adj, rmax, entry, max_visits, queries, nq, k,
+                                     L, ids, dist, visits, hops, qstatus, stream),
+           "roar_search_noalloc")
 
 
 def roar_quantize(X, n, d, dtype, out, scales, stream=None):

@@ -18,6 +18,7 @@ constexpr int kMaxWarpsPerSm = 32;
 #define ROAR_MIN_BLOCKS 5
 #endif
 constexpr int kMinBlocksPerSm = ROAR_MIN_BLOCKS;  // register budget: 65536 / (blocks * 128)
+#define ROAR_NOALLOC_SCRATCH_BYTES (64ull << 20)
 
 // Everything one search launch needs. Plain pointers: the launch reads the
 // index rows, the queries and the scratch, and writes the result arrays.
