@@ -220,6 +220,49 @@ def _cpu_baseline(X, adj_np, entry, Q, L, budget_s=12.0):
                       f"on {cores} threads"}
 
 
+def _serve_rate(srv, Qpool, rate, duration, seed_tag):
+    """Open-loop Poisson stream at `rate` queries/s: requests of 1..256 queries,
+    k in {10, 100}, L in [50, 400]. Latency = arrival to completion (includes
+    any wait for admission)."""
+    import roarsynth as rs
+
+    t_arr, sizes, ks, Ls = rs.poisson_requests(rate, duration, seed_tag=seed_tag)
+    n = len(t_arr)
+    pending = {}
+    lats = []
+    done_q = 0
+    i, qoff = 0, 0
+    start = time.perf_counter()
+    t_last = start
+    deadline = start + duration + 30.0
+    while (i < n or pending) and time.perf_counter() < deadline:
+        now = time.perf_counter() - start
+        while i < n and t_arr[i] <= now:
+            nq = int(sizes[i])
+            if qoff + nq > len(Qpool):
+                qoff = 0
+            rid = srv.submit(Qpool[qoff:qoff + nq], int(ks[i]), int(Ls[i]))
+            if rid is None:
+                break                       # ring full: admission waits
+            pending[rid] = (nq, int(ks[i]), t_arr[i], now)
+            qoff += nq
+            i += 1
+        for rid in list(pending):
+            nq, k, ta, tsub = pending[rid]
+            r = srv.poll(rid, nq, k, timeout_ms=0, want_results=False)
+            if r is not None:
+                lats.append((tsub - ta) + r[0])
+                done_q += nq
+                t_last = time.perf_counter()
+                del pending[rid]
+    span = max(1e-9, t_last - start)
+    lats = np.asarray(lats)
+    return {"offered_qps": rate, "achieved_qps": done_q / span, "requests": int(len(lats)),
+            "queries": int(done_q), "p50_ms": float(np.percentile(lats, 50) * 1e3) if len(lats) else None,
+            "p99_ms": float(np.percentile(lats, 99) * 1e3) if len(lats) else None,
+            "unfinished_requests": int(n - len(lats))}
+
+
 def _traffic(kernel_file, src_hash):
     """ncu DRAM bytes per launch from the committed profile summary, if it
     was taken on the current kernel source; else None."""
@@ -405,6 +448,22 @@ def main():
         plan.close()
         del Qud, uout
 
+    # ---- serving: continuous batching into the persistent kernel ------------------
+    serving = None
+    if not args.no_forms:
+        sidx = pkg.Index(Xd, adj, entry, max_visits=16384)
+        sidx.autotune(Qd, 10, 400, repeats=1)
+        srv = pkg.Server(sidx, k_max=100, L_max=400, ring_capacity=1 << 16, idle_ms=50)
+        Qpool = rs.test_queries(rs.scaled(w, n_test=65536))
+        serving = {"index": w.name, "requests": "Poisson arrivals; 1..256 queries; k in {10,100}; "
+                                              "L in [50,400]", "rates": []}
+        for j, rate in enumerate((1e4, 3e4, 1e5, 3e5, 1e6)):
+            serving["rates"].append(_serve_rate(srv, Qpool, rate, 1.0, 200 + j))
+            log(f"serving {serving['rates'][-1]}")
+        serving["server"] = srv.stats()
+        srv.close()
+        sidx.close()
+
     cpu = None
     if rank == 0:
         cpu = _cpu_baseline(X, adj.cpu().numpy().view(np.uint32), entry, Q, L)
@@ -426,6 +485,7 @@ def main():
         "clocks": clk.summary(),
         "forms": forms,
         "uneven": uneven,
+        "serving": serving,
         "sweep": {str(k): v for k, v in sweep.items()},
         "build": bstats,
     }

@@ -52,6 +52,17 @@ typedef enum {
 
 typedef struct roar_index roar_index;
 typedef struct roar_plan roar_plan;
+typedef struct roar_server roar_server;
+
+/* Serving-loop configuration (roar_server_create). */
+typedef struct {
+    int32_t ring_capacity;  /* query slots that may be in flight; 0: from memory_budget */
+    int64_t memory_budget;  /* bytes of in-flight state when ring_capacity == 0 (0: 65536 slots) */
+    int32_t k_max;          /* largest k of a request */
+    int32_t L_max;          /* largest L of a request (sizes each team's pool) */
+    int32_t team_warps;     /* warps per query team, 0: the handle's tuning for L_max */
+    int32_t idle_ms;        /* the kernel exits after this long without work (0: 50 ms) */
+} roar_server_cfg;
 
 /* Text for a status code (static storage). */
 const char *roar_status_string(roar_status s);
@@ -227,6 +238,48 @@ roar_status roar_search_noalloc(int64_t n, int32_t d, const float *base_f32, con
                                 const float *queries, int64_t nq, int32_t k, int32_t L,
                                 uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops,
                                 int32_t *qstatus, void *stream);
+
+/*
+ * Serving loop (continuous batching; no counterpart in the paper, whose
+ * search runs one query at a time, Sec. 5.1). A server keeps the handle's
+ * index resident and runs one persistent search kernel whose teams take
+ * queries from a ring of slots in mapped pinned host memory as they are
+ * published, so requests that arrive while others run start as soon as a
+ * team is free. Every query is the beam search of roar_search with its
+ * request's k and L, bit-identical to searching it alone.
+ * Admission: the ring holds ring_capacity queries (or memory_budget / (4d +
+ * 8 k_max + 8 L_max + 24) when 0); a request that does not fit is refused
+ * with ROAR_EBUSY and may be retried after polls release slots.
+ * The kernel's teams exit after idle_ms without work and the server
+ * relaunches it when work is waiting; every wait in the kernel is bounded.
+ * The server uses the handle's scratch: do not search the same handle while
+ * a server runs on it. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ */
+roar_status roar_server_create(roar_index *idx, const roar_server_cfg *cfg, roar_server **out);
+
+/*
+ * Submit nq queries (host [nq][d] FP32, copied) with one k and L. On success
+ * *request_id identifies the request. ROAR_EBUSY: not enough free slots now.
+ */
+roar_status roar_server_submit(roar_server *srv, const float *q_host, int32_t nq, int32_t k, int32_t L,
+                               uint64_t *request_id);
+
+/*
+ * Wait up to timeout_ms for a request. When complete: copies results to the
+ * host arrays given (ids/dist [nq][k], visits/qstatus [nq]; any may be NULL),
+ * writes the submit-to-completion latency in seconds, releases its slots and
+ * returns ROAR_OK. ROAR_ETIMEOUT if not complete in time (poll again later);
+ * ROAR_EINVAL for an unknown or already released request.
+ */
+roar_status roar_server_poll(roar_server *srv, uint64_t request_id, int32_t timeout_ms, uint32_t *ids,
+                             float *dist, uint32_t *visits, int32_t *qstatus, double *latency_s);
+
+/* out[8]: ring capacity, queries submitted, completed, released, kernel
+ * launches, CTAs per launch, warps per team, kernel running (0/1). */
+roar_status roar_server_stats(roar_server *srv, double *out);
+
+/* Stop the kernel (bounded), join the poller and free the server. NULL is ignored. */
+void roar_server_destroy(roar_server *srv);
 
 /*
  * Reduced-precision copy of base rows for the traversal (a compression the

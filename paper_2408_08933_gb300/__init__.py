@@ -20,6 +20,13 @@ DTYPE_CODES = {"f32": ROAR_F32, "bf16": ROAR_BF16, "fp8": ROAR_FP8_E4M3}
 _lib = None
 
 
+class ServerCfg(ctypes.Structure):
+    """roar_server_cfg (include/roargraph.h)."""
+    _fields_ = [("ring_capacity", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
+                ("k_max", ctypes.c_int32), ("L_max", ctypes.c_int32), ("team_warps", ctypes.c_int32),
+                ("idle_ms", ctypes.c_int32)]
+
+
 class RoarError(RuntimeError):
     def __init__(self, status: int, where: str):
         lib_ = _lib
@@ -69,6 +76,16 @@ def lib() -> ctypes.CDLL:
     L.roar_search_noalloc.argtypes = [i64, i32, P, P, i32, u32, u32, P, i64, i32, i32, P, P, P, P,
                                       P, P]
     L.roar_search_noalloc.restype = ctypes.c_int
+    L.roar_server_create.argtypes = [P, ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]
+    L.roar_server_create.restype = ctypes.c_int
+    L.roar_server_submit.argtypes = [P, P, i32, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+    L.roar_server_submit.restype = ctypes.c_int
+    L.roar_server_poll.argtypes = [P, ctypes.c_uint64, i32, P, P, P, P, ctypes.POINTER(ctypes.c_double)]
+    L.roar_server_poll.restype = ctypes.c_int
+    L.roar_server_stats.argtypes = [P, P]
+    L.roar_server_stats.restype = ctypes.c_int
+    L.roar_server_destroy.argtypes = [P]
+    L.roar_server_destroy.restype = None
     L.roar_quantize.argtypes = [P, i64, i32, ctypes.c_int, P, P, P]
     L.roar_quantize.restype = ctypes.c_int
     L.roar_knn.argtypes = [P, i64, P, i64, i32, i32, P, P, P]
@@ -155,6 +172,45 @@ def roar_search_noalloc(n, d, base_f32, adj, rmax, entry, max_visits, queries, n
     _check(lib().roar_search_noalloc(n, d, base_f32, adj, rmax, entry, max_visits, queries, nq, k,
                                      L, ids, dist, visits, hops, qstatus, stream),
            "roar_search_noalloc")
+
+
+def roar_server_create(handle, cfg):
+    p = ctypes.c_void_p()
+    _check(lib().roar_server_create(handle, ctypes.byref(cfg), ctypes.byref(p)), "roar_server_create")
+    return p.value
+
+
+def roar_server_submit(srv, q_host, nq, k, L):
+    """Returns the request id, or None when the ring has no room (ROAR_EBUSY)."""
+    rid = ctypes.c_uint64()
+    st = lib().roar_server_submit(srv, q_host, nq, k, L, ctypes.byref(rid))
+    if st == ROAR_EBUSY:
+        return None
+    _check(st, "roar_server_submit")
+    return rid.value
+
+
+def roar_server_poll(srv, request_id, timeout_ms, ids=None, dist=None, visits=None, qstatus=None):
+    """Returns the latency in seconds when complete, None on ROAR_ETIMEOUT."""
+    lat = ctypes.c_double()
+    st = lib().roar_server_poll(srv, request_id, timeout_ms, ids, dist, visits, qstatus, ctypes.byref(lat))
+    if st == ROAR_ETIMEOUT:
+        return None
+    _check(st, "roar_server_poll")
+    return lat.value
+
+
+def roar_server_stats(srv):
+    import numpy as np
+
+    out = np.zeros(8, dtype=np.float64)
+    _check(lib().roar_server_stats(srv, out.ctypes.data), "roar_server_stats")
+    return dict(zip(["ring", "submitted", "completed", "released", "launches", "blocks", "team_warps",
+                     "running"], out.tolist()))
+
+
+def roar_server_destroy(srv):
+    lib().roar_server_destroy(srv)
 
 
 def roar_quantize(X, n, d, dtype, out, scales, stream=None):
@@ -361,6 +417,53 @@ class Plan:
     def close(self):
         if self.handle:
             roar_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching search server over an Index (see roar_server_create)."""
+
+    def __init__(self, index, k_max=100, L_max=400, ring_capacity=0, memory_budget=0, team_warps=0,
+                 idle_ms=50):
+        self.index = index
+        cfg = ServerCfg(ring_capacity, memory_budget, k_max, L_max, team_warps, idle_ms)
+        self.handle = roar_server_create(index.handle, cfg)
+        self.d = index.d
+
+    def submit(self, q, k, L):
+        """q: float32 numpy [nq, d]; returns a request id or None if the ring is full."""
+        import numpy as np
+
+        q = np.ascontiguousarray(q, dtype=np.float32)
+        return roar_server_submit(self.handle, q.ctypes.data, q.shape[0], k, L)
+
+    def poll(self, rid, nq, k, timeout_ms=0, want_results=True):
+        """Returns (latency_s, ids, dist, visits, status) when complete, else None."""
+        import numpy as np
+
+        if want_results:
+            ids = np.empty((nq, k), np.uint32)
+            dist = np.empty((nq, k), np.float32)
+            vis = np.empty(nq, np.uint32)
+            st = np.empty(nq, np.int32)
+            lat = roar_server_poll(self.handle, rid, timeout_ms, ids.ctypes.data, dist.ctypes.data,
+                                   vis.ctypes.data, st.ctypes.data)
+            return None if lat is None else (lat, ids, dist, vis, st)
+        lat = roar_server_poll(self.handle, rid, timeout_ms)
+        return None if lat is None else (lat, None, None, None, None)
+
+    def stats(self):
+        return roar_server_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            roar_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -47,6 +47,15 @@ struct SearchArgs {
     uint32_t *vlog;          // per-warp-slot log of the ids set in the bitmap, vlog_cap each
     int32_t vlog_cap;
     unsigned int *work;      // next unclaimed query (reset per launch)
+    // Serving ring (all null for batch launches): queries, k, L and result
+    // slots are indexed by slot = sequence % ring_cap.
+    const volatile unsigned long long *ring_tail;  // mapped host: requests published so far
+    unsigned long long *ring_head;                 // device: requests claimed so far
+    volatile uint32_t *ring_done;                  // mapped host: per slot, low 32 bits of seq + 1 when done
+    const volatile int *ring_stop;                 // mapped host: nonzero asks the kernel to exit
+    int64_t ring_cap;
+    int32_t ring_kmax;                             // result slots per ring entry
+    uint32_t idle_polls;                           // empty polls (about 1 us apart) before exiting
     uint32_t *ids;
     float *dist;
     uint32_t *visits;
@@ -73,5 +82,9 @@ template <int DT>
 const void *kernel_table(int nch, int rpl, int tw);
 
 int hash_log2_for(int L);
+
+// Fills a SearchArgs for a handle (index rows, tuning, scratch sized for the
+// full resident grid) and picks blocks and team warps. Defined in roar_capi.cu.
+roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &blocks, int &tw, int64_t nq);
 
 }  // namespace roar

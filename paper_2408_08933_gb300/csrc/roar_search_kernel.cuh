@@ -270,20 +270,57 @@ beam_search_kernel(const SearchArgs a) {
         }
     };
 
+    const bool serving = a.ring_tail != nullptr;
     for (;;) {
-        if (leader && lane == 0) ctl[0] = (int)atomicAdd(a.work, 1u);
+        if (leader && lane == 0) {
+            if (!serving) {
+                ctl[0] = (int)atomicAdd(a.work, 1u);
+            } else {
+                // Claim the next published request; bounded idle polling.
+                long long got = -1;
+                for (uint32_t spin = 0;; ++spin) {
+                    if (*a.ring_stop) break;
+                    const unsigned long long h = *reinterpret_cast<volatile unsigned long long *>(a.ring_head);
+                    const unsigned long long t = *a.ring_tail;
+                    if (h < t) {
+                        if (atomicCAS(a.ring_head, h, h + 1) == h) {
+                            got = (long long)h;
+                            break;
+                        }
+                        continue;
+                    }
+                    if (spin >= a.idle_polls) break;
+                    __nanosleep(1000);
+                }
+                __threadfence_system();  // request data was published before the tail
+                ctl[0] = (int)(got & 0xFFFFFFFF);
+                ctl[3] = (int)(got >> 32);
+            }
+        }
         tsync();
-        const int64_t claim = (int64_t)(unsigned)ctl[0];
-        if (claim >= a.nq) break;
-        const int64_t qi = a.order ? (int64_t)a.order[claim] : claim;
-        const int k = a.k_arr ? a.k_arr[qi] : a.k;
-        const int L = a.L_arr ? a.L_arr[qi] : a.L;
-        const int64_t ooff = a.out_off ? a.out_off[qi] : qi * (int64_t)k;
-        if (L < 1 || L > lcap || k < 1 || k > L) {  // a bad per-query (k, L): report, skip
+        int64_t claim, qi;
+        if (!serving) {
+            claim = (int64_t)(unsigned)ctl[0];
+            if (claim >= a.nq) break;
+            qi = a.order ? (int64_t)a.order[claim] : claim;
+        } else {
+            claim = (int64_t)(((unsigned long long)(unsigned)ctl[3] << 32) | (unsigned)ctl[0]);
+            if (claim < 0) break;
+            qi = claim % a.ring_cap;
+        }
+        // Serving inputs change between requests in a slot: read them coherently.
+        const int k = serving ? *(const volatile int32_t *)(a.k_arr + qi) : (a.k_arr ? a.k_arr[qi] : a.k);
+        const int L = serving ? *(const volatile int32_t *)(a.L_arr + qi) : (a.L_arr ? a.L_arr[qi] : a.L);
+        const int64_t ooff = serving ? qi * (int64_t)a.ring_kmax : (a.out_off ? a.out_off[qi] : qi * (int64_t)k);
+        if (L < 1 || L > lcap || k < 1 || k > L || (serving && k > a.ring_kmax)) {  // bad (k, L): report, skip
             if (leader && lane == 0) {
                 if (a.visits) a.visits[qi] = 0;
                 if (a.hops) a.hops[qi] = 0;
                 if (a.qstatus) a.qstatus[qi] = ROAR_EINVAL;
+                if (serving) {
+                    __threadfence_system();
+                    a.ring_done[qi] = (uint32_t)(claim + 1);
+                }
             }
             continue;
         }
@@ -293,7 +330,7 @@ beam_search_kernel(const SearchArgs a) {
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             const int ch = lane + 32 * c;
-            qr[c] = ch < d4 ? __ldg(q4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+            qr[c] = ch < d4 ? (serving ? __ldcv(q4 + ch) : __ldg(q4 + ch)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // Leader-only search state.
         int size = 1, cursor = 0, nlog = 0;
@@ -521,10 +558,16 @@ beam_search_kernel(const SearchArgs a) {
             }
         }
         if (leader) {
+            if (serving) __threadfence_system();  // every lane's result writes, before the done mark
+            __syncwarp();
             if (lane == 0) {
                 if (a.visits) a.visits[qi] = visits;
                 if (a.hops) a.hops[qi] = hops;
                 if (a.qstatus) a.qstatus[qi] = overflow ? ROAR_EOVERFLOW : (bad ? ROAR_EINVAL : ROAR_OK);
+                if (serving) {  // results are visible to the host before the done mark
+                    __threadfence_system();
+                    a.ring_done[qi] = (uint32_t)(claim + 1);
+                }
             }
             // Return the bitmap to all-zero: clear every word this query set.
             for (int i = lane; i < nlog; i += 32) atomicAnd(bits + (vlog[i] >> 5), 0u);

@@ -1,0 +1,115 @@
+"""Serving loop: continuous batching into one persistent search kernel.
+
+Each query served in a mixed stream is bit-identical to searching it alone
+(the paper's beam search, Sec. 4.3, with its request's k and L)."""
+import time
+
+import numpy as np
+import pytest
+
+import paper_2408_08933_gb300 as pkg
+import roarsynth as rs
+from gpu_util import dev_index, run
+
+pytestmark = pytest.mark.gpu
+MV = 16384
+
+
+@pytest.fixture(scope="module")
+def two_handles(tiny):
+    serve = dev_index(tiny["X"], tiny["adj"], tiny["entry"], max_visits=MV)
+    ref = dev_index(tiny["X"], tiny["adj"], tiny["entry"], max_visits=MV)
+    yield serve, ref
+    serve.close()
+    ref.close()
+
+
+def _drain(srv, pending, timeout_s=30.0):
+    out = {}
+    t_end = time.time() + timeout_s
+    while pending and time.time() < t_end:
+        for rid in list(pending):
+            nq, k = pending[rid]
+            r = srv.poll(rid, nq, k, timeout_ms=0)
+            if r is not None:
+                out[rid] = r
+                del pending[rid]
+        time.sleep(0.0005)
+    assert not pending, f"{len(pending)} requests never completed"
+    return out
+
+
+def test_mixed_stream_equals_alone(tiny, two_handles):
+    serve, ref = two_handles
+    srv = pkg.Server(serve, k_max=100, L_max=400, ring_capacity=4096, idle_ms=20)
+    _, sizes, ks, Ls = rs.poisson_requests(3e5, 0.002, seed_tag=41, size_range=(1, 40))
+    Q = tiny["Q"]
+    pending, meta, qpos = {}, {}, 0
+    for nq, k, L in zip(sizes, ks, Ls):
+        nq = int(nq)
+        q = Q[qpos % 900: qpos % 900 + nq]
+        nq = q.shape[0]
+        rid = srv.submit(q, int(k), int(L))
+        assert rid is not None
+        pending[rid] = (nq, int(k))
+        meta[rid] = (q, int(k), int(L))
+        qpos += nq
+    results = _drain(srv, pending)
+    for rid, (lat, ids, dist, vis, st) in results.items():
+        q, k, L = meta[rid]
+        alone = run(ref, q, k, L)
+        assert np.array_equal(ids, alone[0]) and np.array_equal(dist, alone[1])
+        assert np.array_equal(vis, alone[2]) and np.array_equal(st, alone[4])
+        assert lat > 0
+    s = srv.stats()
+    assert s["completed"] == s["submitted"] == qpos
+    srv.close()
+
+
+def test_admission_refuses_when_ring_is_full(tiny, two_handles):
+    serve, _ = two_handles
+    srv = pkg.Server(serve, k_max=10, L_max=64, ring_capacity=64, idle_ms=20)
+    Q = tiny["Q"]
+    assert srv.submit(Q[:65], 10, 32) is None          # larger than the ring
+    a = srv.submit(Q[:64], 10, 32)
+    assert a is not None
+    assert srv.submit(Q[:1], 10, 32) is None           # no room until released
+    r = None
+    t_end = time.time() + 10
+    while r is None and time.time() < t_end:
+        r = srv.poll(a, 64, 10, timeout_ms=50)
+    assert r is not None
+    assert srv.submit(Q[:1], 10, 32) is not None       # released slots are reused
+    with pytest.raises(pkg.RoarError):
+        srv.poll(a, 64, 10, timeout_ms=0)              # already released
+    with pytest.raises(pkg.RoarError):
+        srv.submit(Q[:1], 20, 32)                       # k above k_max
+    srv.close()
+
+
+def test_idle_exit_and_relaunch(tiny, two_handles):
+    serve, ref = two_handles
+    srv = pkg.Server(serve, k_max=10, L_max=64, ring_capacity=256, idle_ms=5)
+    Q = tiny["Q"]
+    a = srv.submit(Q[:8], 10, 50)
+    r = _drain(srv, {a: (8, 10)})
+    time.sleep(0.2)                                     # teams exit after 5 ms idle
+    s = srv.stats()
+    assert s["running"] == 0.0
+    b = srv.submit(Q[8:16], 10, 50)
+    r2 = _drain(srv, {b: (8, 10)})
+    assert srv.stats()["launches"] >= 2
+    assert np.array_equal(r2[b][1], run(ref, Q[8:16], 10, 50)[0])
+    srv.close()
+
+
+def test_poll_timeout_is_bounded(tiny, two_handles):
+    serve, _ = two_handles
+    srv = pkg.Server(serve, k_max=10, L_max=400, ring_capacity=2048, idle_ms=20)
+    rid = srv.submit(tiny["Q"][:1000], 10, 400)
+    t0 = time.time()
+    first = srv.poll(rid, 1000, 10, timeout_ms=0)      # may or may not be done yet
+    assert time.time() - t0 < 1.0
+    if first is None:
+        assert _drain(srv, {rid: (1000, 10)})
+    srv.close()
