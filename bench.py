@@ -97,6 +97,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The job's time is the slowest rank's (replicas: no other exchange).
+    Without an initialised process group this is the value itself."""
+    import torch
+    import torch.distributed as tdist
+
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _src_hash(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -333,7 +346,7 @@ def main():
               "k": 10, "L": L, "recall_at_10": sweep[L]["recall"], "recall_target": TARGET_RECALL,
               "recall_target_reached": reached, "batch": nq,
               "launch": {"variant": best, "team_warps": [1, 2, 4, 8][best // 4] if best >= 0 else None,
-                         "visited_table": ["auto", "bitmap", "2^10", "2^12"][best % 4] if best >= 0 else None},
+                         "visited_set": ["auto", "bitmap", "2^10 shared + bitmap", "2^12 shared + bitmap"][best % 4] if best >= 0 else None},
               "l2_flush": "not needed: base rows 800 MB > 129 MB L2", "parallelism": f"replicas x{world}"}
 
     if args.impl == "reference":
@@ -363,11 +376,7 @@ def main():
         torch.cuda.nvtx.range_pop()
     if dist_on:
         tdist.barrier()
-    total_ms = sum(ms)
-    if dist_on:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), dev if dist_on else None)
     ids, dist, visits, hops, st = out
     value = world * nq * args.steps / (total_ms / 1e3)
 
@@ -378,7 +387,8 @@ def main():
     avg_ms = total_ms / args.steps
     achieved = bytes_q * nq / (avg_ms / 1e3) / 1e9
     peak, peak_src = _peaks()
-    src_hash = _src_hash(["paper_2408_08933_gb300/csrc/roar_search.cu"])
+    src_hash = _src_hash(["paper_2408_08933_gb300/csrc/roar_search_kernel.cuh",
+                          "paper_2408_08933_gb300/csrc/roar_search.cu"])
     traffic = _traffic(f"search_f32_{w.name}.txt", src_hash)
 
     # ---- e2e: host buffers through roar_search_host -----------------------------
