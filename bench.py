@@ -295,6 +295,125 @@ def _traffic(kernel_file, src_hash):
         return None
 
 
+def _time_once(fn, torch, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bstats, log):
+    """The precision (10M x 512), uneven (1M x 512) and serving (10M x 200) workloads."""
+    nq = Q.shape[0]
+    res = {"mode": args.mode, "workload": w.name, "n": w.n, "d": w.d, "build": bstats}
+    forms = {}
+    if args.mode == "precision":
+        sweepL = [50, 100, 200, 500, 1024]
+        sample = np.random.default_rng(1).choice(nq, 200, replace=False)
+        for dtype in ("f32", "bf16", "fp8"):
+            if dtype == "f32":
+                idx = pkg.Index(Xd, adj, entry, max_visits=16384)
+                codes = sc = None
+            else:
+                codes, sc = pkg.quantize(Xd, dtype)
+                idx = pkg.Index(Xd, adj, entry, dtype=dtype, trav=codes, scales=sc, max_visits=16384)
+            rows = {}
+            for L in sweepL:
+                ms = _time_once(lambda: idx.search(Qd, 10, L), torch)
+                ids, dist, visits, hops, st = idx.search(Qd, 10, L)
+                torch.cuda.synchronize()
+                ids_h = ids.cpu().numpy().view(np.uint32)
+                rows[L] = {"qps": nq / (ms / 1e3), "recall_at_10": _recall(ids_h, gt),
+                           "visits": float(visits.double().mean()), "hops": float(hops.double().mean())}
+                if L == 500:
+                    # per-result distance error vs FP64, on 200 sampled queries
+                    dh = dist.cpu().numpy()[sample]
+                    ih = ids_h[sample]
+                    ref = -np.einsum("qkd,qd->qk", X[ih].astype(np.float64), Q[sample].astype(np.float64))
+                    err = np.abs(dh.astype(np.float64) - ref)
+                    rows[L]["result_dist_err_vs_fp64"] = {"max": float(err.max()), "mean": float(err.mean())}
+                    if codes is not None:
+                        sel = torch.from_numpy(ih.ravel().astype(np.int64)).to(dev)
+                        ch = codes[sel].cpu().numpy()
+                        if dtype == "bf16":
+                            dec = (ch.view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+                        else:
+                            import torch as _t
+                            dec = _t.from_numpy(ch).view(_t.float8_e4m3fn).double().numpy()
+                            dec *= sc[sel].cpu().numpy().astype(np.float64)[:, None]
+                        trav = -(dec.reshape(len(sample), 10, -1) * Q[sample].astype(np.float64)[:, None, :]).sum(-1)
+                        terr = np.abs(trav - ref)
+                        rows[L]["traversal_dist_err_vs_fp64"] = {"max": float(terr.max()), "mean": float(terr.mean())}
+                log(f"{dtype} L={L}: {rows[L]}")
+            forms[dtype] = rows
+            idx.close()
+            del codes, sc
+        for dtype in ("bf16", "fp8"):
+            for L in sweepL:
+                forms[dtype][L]["recall_delta_vs_f32"] = forms[dtype][L]["recall_at_10"] - forms["f32"][L]["recall_at_10"]
+        res["forms"] = {k: {str(L): v for L, v in rows.items()} for k, rows in forms.items()}
+    elif args.mode == "uneven":
+        codes, sc = pkg.quantize(Xd, "bf16")
+        idx = pkg.Index(Xd, adj, entry, dtype="bf16", trav=codes, scales=None, max_visits=16384)
+        nu = 65536
+        Qu = rs.test_queries(rs.scaled(w, n_test=nu))
+        ku, Lu = rs.uneven_params(nu, seed_tag=7)
+        Qud, kud, Lud = (torch.from_numpy(a).to(dev) for a in (Qu, ku, Lu))
+        table = {}
+        for Lb in (32, 64, 128, 256, 512):
+            best, ms = idx.autotune(Qud[:8192], 10, Lb, repeats=1)
+            table[str(Lb)] = {"best_variant": int(best), "team_warps": [1, 2, 4, 8][best // 4],
+                              "ms": [round(float(x), 3) if x < 1e29 else None for x in ms]}
+        out = idx.uneven_outputs(ku)
+        plan = idx.plan_uneven(Qud, kud, Lud, int(Lu.max()), out, longest_first=True)
+        ms = _time_once(plan.launch, torch, reps=5)
+        offs = out[0].cpu().numpy()
+        mixed = out[1].cpu().numpy().view(np.uint32)
+        same = True
+        for i in np.random.default_rng(2).choice(nu, 64, replace=False):
+            ids, *_ = idx.search(Qud[i:i + 1], int(ku[i]), int(Lu[i]))
+            torch.cuda.synchronize()
+            same &= ids.cpu().numpy().view(np.uint32)[0].tolist() == mixed[offs[i]:offs[i] + ku[i]].tolist()
+        res.update({"queries": nu, "ms_per_launch": ms, "qps": nu / (ms / 1e3), "autotune": table,
+                    "alone_equals_mixed_on_64_samples": bool(same), "form": "bf16 traversal + fp32 re-rank",
+                    "graph_captured": True})
+        plan.close()
+        idx.close()
+    elif args.mode == "serving":
+        codes, sc = pkg.quantize(Xd, "bf16")
+        sidx = pkg.Index(Xd, adj, entry, dtype="bf16", trav=codes, scales=None, max_visits=16384)
+        sidx.autotune(Qd, 10, 400, repeats=1)
+        srv = pkg.Server(sidx, k_max=100, L_max=400, ring_capacity=1 << 16, idle_ms=50)
+        Qpool = rs.test_queries(rs.scaled(w, n_test=65536))
+        rates = []
+        for j, rate in enumerate((1e4, 3e4, 1e5, 3e5, 1e6)):
+            rates.append(_serve_rate(srv, Qpool, rate, 1.0, 300 + j))
+            log(f"serving {rates[-1]}")
+        # recall of served results for the 10k test queries at L = 400
+        rids = []
+        for i in range(0, nq, 256):
+            rid = None
+            while rid is None:
+                rid = srv.submit(Q[i:i + 256], 10, 400)
+            rids.append((rid, min(256, nq - i)))
+        got = []
+        for rid, m in rids:
+            r = None
+            while r is None:
+                r = srv.poll(rid, m, 10, timeout_ms=100)
+            got.append(r[1])
+        res.update({"form": "bf16 traversal + fp32 re-rank", "rates": rates,
+                    "served_recall_at_10_L400": _recall(np.concatenate(got), gt), "server": srv.stats()})
+        srv.close()
+        sidx.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,8 +421,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="base_1m_d200")
-    ap.add_argument("--n", type=int, default=0, help="override base rows (debug)")
+    ap.add_argument("--n", type=int, default=0, help="override base rows (smaller runs)")
+    ap.add_argument("--n-train", type=int, default=0, help="override training queries")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving"],
+                    help="main: the benchmark line; others: the precision / uneven / serving workloads")
     ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -332,8 +454,14 @@ def main():
         tdist.init_process_group("nccl")
     w = rs.WORKLOADS[args.workload]
     if args.n:
-        w = rs.scaled(w, n=args.n, n_train=args.n)
+        w = rs.scaled(w, n=args.n, n_train=args.n_train or min(args.n, w.n_train))
+    elif args.n_train:
+        w = rs.scaled(w, n_train=args.n_train)
     dev, X, Q, Xd, Qd, adj, entry, gt, bstats = _setup(w, torch, pkg, rs, log)
+    if args.mode != "main":
+        out = _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bstats, log)
+        print(json.dumps(out), flush=True)
+        return
     idx = pkg.Index(Xd, adj, entry, max_visits=16384)
     sweep = _sweep(idx, Qd, gt, torch, L_SWEEP)
     L, reached = _pick_L(sweep)

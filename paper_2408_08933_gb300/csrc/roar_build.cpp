@@ -26,6 +26,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 #include <utility>
@@ -127,7 +128,9 @@ struct Lists {
 // appends a reverse edge whenever the list has room, so its lists end up full
 // of reverse edges after each pruning, and the top-up gives the batched round
 // the same outcome.
-void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lists &fwd) {
+// A node that many lists point to (a hub) keeps at most `max_in` of its
+// reverse-edge candidates, the nearest ones, before pruning.
+void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lists &fwd, int max_in) {
     const int64_t n = fwd.n;
     std::vector<int64_t> off((size_t)n + 1, 0);
     for (int64_t x = 0; x < n; ++x)
@@ -143,10 +146,11 @@ void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lis
         const uint32_t *f = fwd.row(p);
         const int nf = fwd.cnt[p];
         std::vector<uint32_t> all(f, f + nf);
+        // Incoming ids are distinct and ascending; only the own list can repeat them.
         for (int64_t k = off[p]; k < off[p + 1]; ++k) {
             const uint32_t x = inc[k];
             if (x == (uint32_t)p) continue;
-            if (std::find(all.begin(), all.end(), x) == all.end()) all.push_back(x);
+            if (std::find(f, f + nf, x) == f + nf) all.push_back(x);
         }
         uint32_t *o = out.row(p);
         if ((int)all.size() <= M) {
@@ -158,6 +162,12 @@ void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lis
         C.reserve(all.size());
         const float *pv = X + (size_t)p * d;
         for (uint32_t c : all) C.emplace_back(neg_dot(pv, X + (size_t)c * d, d), c);
+        if ((int)C.size() > nf + max_in) {  // keep the own list and the nearest reverse edges
+            std::vector<Cand> own(C.begin(), C.begin() + nf);
+            std::nth_element(C.begin() + nf, C.begin() + nf + max_in, C.end(), cand_less);
+            C.resize((size_t)(nf + max_in));
+            std::copy(own.begin(), own.end(), C.begin());
+        }
         std::sort(C.begin(), C.end(), cand_less);
         int r = acquire(X, d, (uint32_t)p, C, M, fill, o);
         if (!fill) {
@@ -175,6 +185,16 @@ void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lis
 
 double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Progress lines on stderr when ROAR_BUILD_LOG is set (long builds).
+void build_log(const char *fmt, double a = 0, double b = 0, double c = 0) {
+    static const bool on = std::getenv("ROAR_BUILD_LOG") != nullptr;
+    if (!on) return;
+    std::fprintf(stderr, "[roar_build] ");
+    std::fprintf(stderr, fmt, a, b, c);
+    std::fprintf(stderr, "\n");
+    std::fflush(stderr);
 }
 
 // BFS from entry over [n][R] adjacency; returns unreachable ids ascending.
@@ -298,6 +318,7 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         if (rc != ROAR_OK) return rc;
     }
     st[1] = seconds_since(t0);
+    build_log("kNN of %.0f training queries done in %.1f s", (double)nt, st[1]);
 
     // Alg. 1 lines 2-6: base node x = 1-NN(t) gets the edge x -> t.
     t0 = std::chrono::steady_clock::now();
@@ -336,8 +357,36 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         pj.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, true, pj.row(x));
     });
     // Alg. 2 line 9, batched.
-    add_reverse_edges(X.data(), d, M, true, threads, pj);
+    add_reverse_edges(X.data(), d, M, true, threads, pj, 4 * L_build);
+    // The enhancement searches start at the medoid and walk G_pj: a medoid
+    // that no pivot selected has no edges there and every search would stop
+    // at once. Such a medoid gets a list as a pivot would, from its own
+    // nearest base rows (exact kNN on the GPU), with Alg. 3 and fill.
+    if (pj.cnt[entry] == 0) {
+        uint32_t *ki = nullptr;
+        float *kd = nullptr;
+        const int kk = std::min<int64_t>(std::min(128, L_build), n);
+        e = cudaMalloc(&ki, (size_t)kk * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&kd, (size_t)kk * 4);
+        std::vector<uint32_t> hid((size_t)kk);
+        std::vector<float> hd((size_t)kk);
+        if (e == cudaSuccess) rc = roar_knn(X_dev + (size_t)entry * d, 1, X_dev, n, d, kk, ki, kd, stream);
+        if (e == cudaSuccess && rc == ROAR_OK) {
+            e = cudaMemcpy(hid.data(), ki, (size_t)kk * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(hd.data(), kd, (size_t)kk * 4, cudaMemcpyDeviceToHost);
+        }
+        cudaFree(ki);
+        cudaFree(kd);
+        if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: medoid list");
+        if (rc != ROAR_OK) return rc;
+        std::vector<Cand> C;
+        for (int j = 0; j < kk; ++j)
+            if (hid[j] != entry && hid[j] != kNone) C.emplace_back(hd[j], hid[j]);
+        pj.cnt[entry] = acquire(X.data(), d, entry, C, M, true, pj.row(entry));
+        build_log("medoid had no projected edges: gave it %.0f", (double)pj.cnt[entry]);
+    }
     st[2] = seconds_since(t0);
+    build_log("projection done in %.1f s (%.0f pivots)", st[2], (double)pivots.load());
     int64_t pj_edges = 0;
     for (int64_t i = 0; i < n; ++i) pj_edges += pj.cnt[i];
 
@@ -370,6 +419,8 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
                 e = cudaMemcpyAsync(hd.data(), pdist, (size_t)qn * L_build * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) break;
+            build_log("enhancement: searched %.0f of %.0f rows (%.1f s)", (double)(q0 + qn), (double)n,
+                      seconds_since(t0));
             parallel_for(qn, threads, [&](int64_t i, int) {
                 const int64_t x = q0 + i;
                 std::vector<Cand> C;
@@ -392,7 +443,7 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
     st[3] = seconds_since(t0);
     // Alg. 1 line 12 (batched, no fill), then line 14: N_pj followed by the new edges.
     t0 = std::chrono::steady_clock::now();
-    add_reverse_edges(X.data(), d, M, false, threads, ce);
+    add_reverse_edges(X.data(), d, M, false, threads, ce, 4 * L_build);
     std::vector<uint32_t> adj((size_t)n * R, kNone);
     std::vector<int> deg((size_t)n, 0);
     parallel_for(n, threads, [&](int64_t x, int) {
@@ -408,6 +459,7 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         deg[x] = k;
     });
     st[4] = seconds_since(t0);
+    build_log("enhancement done: search+prune %.1f s, reverse+merge %.1f s", st[3], st[4]);
 
     // Reachability repair: each unreachable node gets an edge from the
     // nearest node (among the 16 the search finds from the entry) that still
@@ -420,7 +472,23 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
             std::vector<uint32_t> U = unreachable(adj, n, R, entry);
             if (unreach0 < 0) unreach0 = (int64_t)U.size();
             unreach_final = (int64_t)U.size();
+            build_log("repair round %.0f: %.0f unreachable (%.1f s)", (double)round, (double)U.size(),
+                      seconds_since(t0));
             if (U.empty()) break;
+            if (round >= 3) {
+                // Rare leftovers whose nearby nodes are all full: link each from
+                // any reachable node with a free slot.
+                std::vector<unsigned char> isU((size_t)n, 0);
+                for (uint32_t u : U) isU[u] = 1;
+                int64_t cur = 0;
+                for (uint32_t u : U) {
+                    while (cur < n && (isU[cur] || deg[cur] >= R)) ++cur;
+                    if (cur >= n) break;
+                    adj[(size_t)cur * R + deg[cur]++] = u;
+                    ++repairs;
+                }
+                continue;
+            }
             e = cudaMemcpyAsync(adj_dev, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice, s);
             std::vector<float> Q(U.size() * (size_t)d);
             for (size_t i = 0; i < U.size(); ++i)

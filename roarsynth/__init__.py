@@ -1,8 +1,10 @@
 """Seeded synthetic inputs shaped like RoarGraph's cross-modal workloads.
 
 This module is the one piece shared by the CPU oracle (``oracle/``) and the
-CUDA path (``paper_2408_08933_gb300``): it draws vectors and nothing else.
-It holds none of the method's arithmetic (no distances, no graph, no search).
+CUDA path (``paper_2408_08933_gb300``): it draws random inputs and nothing
+else. It holds none of the method's arithmetic (no distances, no index
+construction, no search); its one graph, ``cluster_graph``, is random
+structure used as a search input.
 
 The paper evaluates on Text-to-Image (10M x 200, inner product), LAION
 (10M x 512, cosine) and WebVid (2.5M x 512, cosine) (Sec. 5.1, Table 1).
@@ -107,7 +109,8 @@ def _rows(w: Workload, array: str, total: int, lo: int, hi: int | None) -> np.nd
     shift = offset(w) if array in ("train", "test") else None
     out = np.empty((hi - lo, w.d), dtype=np.float32)
     c0, c1 = lo // CHUNK, (hi + CHUNK - 1) // CHUNK
-    for c in range(c0, c1):
+
+    def one(c):
         r0, r1 = c * CHUNK, min(total, (c + 1) * CHUNK)
         rng = _rng(w, array, c)
         comp = rng.integers(0, w.n_comp, size=r1 - r0)
@@ -118,7 +121,58 @@ def _rows(w: Workload, array: str, total: int, lo: int, hi: int | None) -> np.nd
         v = _normalize_rows(v)
         a, b = max(lo, r0), min(hi, r1)
         out[a - lo:b - lo] = v[a - r0:b - r0]
+
+    # Chunks are independent streams: generate them on several threads.
+    if c1 - c0 > 2:
+        from concurrent.futures import ThreadPoolExecutor
+        import os
+
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(one, range(c0, c1)))
+    else:
+        for c in range(c0, c1):
+            one(c)
     return out
+
+
+def base_components(w: Workload) -> np.ndarray:
+    """Mixture component of every base row (the same draws as base())."""
+    out = np.empty(w.n, dtype=np.int32)
+    for c in range((w.n + CHUNK - 1) // CHUNK):
+        r0, r1 = c * CHUNK, min(w.n, (c + 1) * CHUNK)
+        out[r0:r1] = _rng(w, "base", c).integers(0, w.n_comp, size=r1 - r0)
+    return out
+
+
+def cluster_graph(w: Workload, local: int = 24, far: int = 8, rmax: int = 64,
+                  seed_tag: int = 9) -> np.ndarray:
+    """A seeded graph with the structure of a navigable index but built
+    without any distance: every node links to `local` random members of its
+    own mixture component and `far` random nodes anywhere. uint32 [n][rmax],
+    duplicates and self loops removed, padded with 0xFFFFFFFF. Used as a
+    search input that comes from neither the oracle nor the CUDA library."""
+    comp = base_components(w)
+    order = np.argsort(comp, kind="stable").astype(np.int64)
+    starts = np.searchsorted(comp[order], np.arange(w.n_comp + 1))
+    ss = np.random.SeedSequence(SEED, spawn_key=(w.tag, 102, seed_tag))
+    rng = np.random.Generator(np.random.PCG64(ss))
+    n = w.n
+    lo = starts[comp]
+    size = starts[comp + 1] - lo
+    cand = np.empty((n, local + far), dtype=np.int64)
+    cand[:, :local] = order[lo[:, None] + (rng.random((n, local)) * size[:, None]).astype(np.int64)]
+    cand[:, local:] = rng.integers(0, n, size=(n, far))
+    cand[cand == np.arange(n)[:, None]] = -1
+    srt = np.sort(cand, axis=1)
+    dup = np.zeros_like(srt, dtype=bool)
+    dup[:, 1:] = srt[:, 1:] == srt[:, :-1]
+    srt[dup] = -1
+    srt = -np.sort(-srt, axis=1)              # valid ids first (descending), -1 at the end
+    adj = np.full((n, rmax), 0xFFFFFFFF, dtype=np.uint32)
+    k = min(rmax, local + far)
+    valid = srt[:, :k] >= 0
+    adj[:, :k][valid] = srt[:, :k][valid].astype(np.uint32)
+    return adj
 
 
 def base(w: Workload, lo: int = 0, hi: int | None = None) -> np.ndarray:
