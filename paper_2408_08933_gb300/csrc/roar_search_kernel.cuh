@@ -196,6 +196,56 @@ __device__ __forceinline__ int smem_visit(uint32_t *tab, int log2, uint32_t u, b
     return 3;
 }
 
+// Insert (cd_, ci_) at slot pos of a sorted pool of `size` entries with
+// capacity L (pos < L, pos <= size): slots pos.. move up by one and the last
+// falls off a full pool. Works on groups of 4 slots per lane (16-byte shared
+// accesses, 128 slots per step) from the top down; the slot that crosses
+// into the group above comes from the next lane by a shuffle (or, for the
+// lowest group of a step, from shared memory below the step, not yet moved).
+__device__ __forceinline__ void pool_insert_one(float *pd, uint32_t *pi, int size, int L, int pos,
+                                                float cd_, uint32_t ci_, int lane) {
+    const int last = min(size, L - 1);  // highest destination slot
+    const int g_lo = pos >> 2, g_hi = last >> 2;
+    float4 *pd4 = reinterpret_cast<float4 *>(pd);
+    uint4 *pi4 = reinterpret_cast<uint4 *>(pi);
+    for (int gb = g_hi; gb >= g_lo; gb -= 32) {
+        const int g = gb - lane;
+        const bool act = g >= g_lo;
+        float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint4 iv = make_uint4(0u, 0u, 0u, 0u);
+        if (act) {
+            dv = pd4[g];
+            iv = pi4[g];
+        }
+        float pdv = __shfl_down_sync(kFull, dv.w, 1);
+        uint32_t piv = __shfl_down_sync(kFull, iv.w, 1);
+        if (act && (lane == 31 || g - 1 < g_lo) && g > 0) {
+            pdv = pd[4 * g - 1];
+            piv = pi[4 * g - 1];
+        }
+        if (act) {
+            const int i0 = 4 * g;
+            float4 nd = dv;
+            uint4 ni = iv;
+            // destination slot i takes the old slot i - 1 for pos < i <= last, the new entry at pos
+#define ROAR_SLOT(J, PREVD, PREVI, DST_D, DST_I)                   \
+    {                                                               \
+        const int i = i0 + J;                                       \
+        if (i == pos) { DST_D = cd_; DST_I = ci_; }                 \
+        else if (i > pos && i <= last) { DST_D = PREVD; DST_I = PREVI; } \
+    }
+            ROAR_SLOT(0, pdv, piv, nd.x, ni.x)
+            ROAR_SLOT(1, dv.x, iv.x, nd.y, ni.y)
+            ROAR_SLOT(2, dv.y, iv.y, nd.z, ni.z)
+            ROAR_SLOT(3, dv.z, iv.z, nd.w, ni.w)
+#undef ROAR_SLOT
+            pd4[g] = nd;
+            pi4[g] = ni;
+        }
+        __syncwarp();
+    }
+}
+
 // Global bitmap visited set: true if u was not yet set.
 __device__ __forceinline__ bool bitmap_visit(uint32_t *bits, uint32_t u) {
     const uint32_t bit = 1u << (u & 31u);
@@ -494,9 +544,24 @@ beam_search_kernel(const SearchArgs a) {
                 cpos[t] = r < cnt ? lower_bound_entries(pd, pi, size, sd[r], si[r]) + r : 0x7FFFFFFF;
             }
             const int pmin = __shfl_sync(kFull, cpos[0], 0);
-            // Move the pool tail [pmin, size) up in place, 32 entries at a time
-            // from the end: new slots are increasing and never below the old
-            // ones, so no write lands on an entry not yet read.
+            if (cnt <= 4) {
+                // Few candidates (the usual case once the pool is full): insert
+                // them one at a time in increasing slot order.
+                int sz = size;
+                for (int r = 0; r < cnt; ++r) {
+                    const int pos = __shfl_sync(kFull, cpos[0], r);
+                    if (pos >= L) break;
+                    pool_insert_one(pd, pi, sz, L, pos, sd[r], si[r], lane);
+                    sz = min(L, sz + 1);
+                }
+                size = sz;
+                cursor = min(cursor, pmin);
+                __syncwarp();
+                continue;
+            }
+            // Many candidates: move the pool tail [pmin, size) up in place, 32
+            // entries at a time from the end: new slots are increasing and never
+            // below the old ones, so no write lands on an entry not yet read.
             for (int hi = size; hi > pmin; hi -= 32) {
                 const int i = hi - 32 + lane;
                 const bool act = i >= pmin;
