@@ -122,8 +122,10 @@ def _setup(w, torch, pkg, rs, log):
     """Generate the workload, build (or load) the index, ground truth and L sweep."""
     dev = torch.device("cuda", torch.cuda.current_device())
     key = _src_hash(["roarsynth/__init__.py", "paper_2408_08933_gb300/csrc/roar_build.cpp",
-                     "paper_2408_08933_gb300/csrc/roar_knn.cu", "paper_2408_08933_gb300/csrc/roar_search.cu"])
-    cache = os.path.join(CACHE_DIR, f"{w.name}_{key}.npz")
+                     "paper_2408_08933_gb300/csrc/roar_knn.cu", "paper_2408_08933_gb300/csrc/roar_knn_tc.cu",
+                     "paper_2408_08933_gb300/csrc/roar_search_kernel.cuh",
+                     "paper_2408_08933_gb300/csrc/roar_search.cu"])
+    cache = os.path.join(CACHE_DIR, f"{w.name}_{w.n}_{w.n_train}_{w.n_test}_{key}.npz")
     t0 = time.time()
     X = rs.base(w)
     Q = rs.test_queries(w)

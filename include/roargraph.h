@@ -299,17 +299,18 @@ roar_status roar_quantize(const float *X, int64_t n, int32_t d, roar_dtype dtype
 /*
  * Exact k-nearest neighbours under delta = -<t, x> (Definition 1, Sec. 2.1.1):
  * the preprocessing step of the construction ("ground truths" of the training
- * queries, Sec. 4.2.1) and the evaluation ground truth. Scores are first
- * computed on the tensor cores (BF16 inputs, FP32 accumulation) to keep each
- * row's 128 best candidates, which are then re-scored with exact FP32 dot
- * products in the search's fixed order; ids/dist get the first kk of them in
- * (distance, id) order.
- *   T [nt][d], X [n][d]   device FP32, 16-byte aligned.
+ * queries, Sec. 4.2.1) and the evaluation ground truth. Scores are computed
+ * on the tensor cores (tcgen05, BF16 inputs, FP32 accumulation in TMEM) with
+ * a fused running selection that keeps each row's 128 best candidates; these
+ * are re-scored with exact FP32 dot products in the search's fixed order and
+ * ids/dist get the first kk in (distance, id) order.
+ *   T [nt][d], X [n][d]   device FP32, 16-byte aligned, d % 8 == 0, d <= 512.
  *   kk                    1..128, kk <= n.
  *   ids, dist             device [nt][kk] outputs.
- * Allocates and frees its own device scratch (BF16 copies of T and X and a
- * score block of up to 4096 x 524288 FP32) and synchronises `stream` before
- * returning. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ * Allocates and frees its own device scratch (BF16 copies of T and X and
+ * candidate buffers of 8 KB per query row for up to 131,072 rows at a time)
+ * and synchronises `stream` before returning. Errors: ROAR_EINVAL,
+ * ROAR_ENOMEM, ROAR_ECUDA, ROAR_ETIMEOUT (a bounded tensor-core wait gave up).
  */
 roar_status roar_knn(const float *T, int64_t nt, const float *X, int64_t n, int32_t d, int32_t kk,
                      uint32_t *ids, float *dist, void *stream);

@@ -19,7 +19,7 @@ CUFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "
                   "-I", CSRC] + os.environ.get("ROAR_NVCC_FLAGS", "").split()
 CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", CSRC,
             "-I", "/usr/local/cuda/include"]
-LDLIBS = ["-L/usr/local/cuda/lib64", "-lcublas", "-lpthread", "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+LDLIBS = ["-lpthread"]
 
 
 def _headers():

@@ -1,0 +1,440 @@
+// Tensor-core scores with a fused running top-C (the kNN step of the index
+// construction, Sec. 4.2.1): S = T . X^T in BF16 with FP32 accumulation on the
+// 5th-generation tensor cores, never written to memory.
+//
+// One CTA owns 128 rows of T (the MMA's M) and keeps them resident in shared
+// memory; it sweeps all rows of X in tiles of 256 (the MMA's N). Warp roles:
+// two producer warps stage 64-wide K chunks of X through a ring of up to four
+// shared-memory stages (cp.async with zero fill past n and d) in the canonical
+// no-swizzle K-major layout (8 x 16-byte core matrices, K-adjacent ones 128 B
+// apart, 8-row groups 1024 B apart); one thread issues tcgen05.mma (kind::f16,
+// BF16 x BF16 -> FP32) into one of two 256-column TMEM accumulators, so the
+// next tile is computed while the last is read; four epilogue warps read their
+// 32 TMEM lanes each (one row per thread) with tcgen05.ld. Per row a running
+// threshold filters the scores: a column enters the row's candidate buffer
+// only if it beats the threshold. Between tiles, a buffer that could not take
+// another full tile is cut back to its best C by its whole warp (a bitwise
+// search for the C-th largest key, then a ballot compaction), which raises the
+// threshold. At the end each row's best C candidates are written out
+// (unsorted) for the exact FP32 re-score.
+//
+// Every mbarrier wait is bounded: on timeout the kernel sets *err, waits for
+// its own copies, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "roar_internal.cuh"
+
+namespace roar {
+
+roar_status cuda_fail(cudaError_t e, const char *what);
+
+namespace {
+
+constexpr int kTM = 128;           // T rows per CTA (MMA M)
+constexpr int kTN = 256;           // X rows per tile (MMA N)
+constexpr int kKC = 64;            // K elements per staged chunk (128 bytes per row)
+constexpr int kProducers = 64;     // warps 0-1 stage operands
+constexpr int kMmaWarp = 2;        // lane 0 issues the MMAs; the warp owns TMEM
+constexpr int kThreads = 7 * 32;
+constexpr int kMaxStages = 4;
+constexpr int kCap = 1024;         // candidate buffer entries per row
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: far above any legitimate wait here
+constexpr int kTmemCols = 512;     // two 256-column accumulators
+constexpr uint32_t kChunkA = kTM * kKC * 2;   // 16 KB
+constexpr uint32_t kChunkB = kTN * kKC * 2;   // 32 KB
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (8-row group)
+// byte offsets (all >> 4), descriptor version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase with the given parity: gives up (and raises the
+// CTA's abort flag) after kWaitNs of wall time, or as soon as another role
+// aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    uint64_t deadline = 0;
+    for (uint32_t i = 0;; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort) return false;
+        if ((i & 63) == 0) {
+            const uint64_t now = global_ns();
+            if (deadline == 0) deadline = now + kWaitNs;
+            else if (now > deadline) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// The barrier's phase completes once this thread's earlier cp.async copies land.
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Order-preserving map of a finite float to uint32 (larger float, larger key).
+__device__ __forceinline__ uint32_t f2key(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float key2f(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// The whole warp cuts one row's buffer (scores s, ids c, m <= kCap entries) to
+// its best `keep` in place and returns the keep-th best score. The keep-th
+// largest key is found bit by bit from the top (the largest t with at least
+// `keep` keys >= t); every key above t is kept, then keys equal to t in buffer
+// order until `keep` are kept. Must be called by all 32 lanes with the same
+// arguments, after the lane that filled the buffer has passed a __syncwarp.
+__device__ float warp_cut(float *s, uint32_t *c, int m, int keep, int lane) {
+    constexpr int kPer = kCap / 32;
+    uint32_t key[kPer], id[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int j = i * 32 + lane;
+        key[i] = j < m ? f2key(s[j]) : 0u;
+        id[i] = j < m ? c[j] : 0u;
+    }
+    uint32_t t = 0;
+    for (int bit = 31; bit >= 0; --bit) {
+        const uint32_t cand = t | (1u << bit);
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) cnt += key[i] >= cand ? 1u : 0u;
+        if ((int)__reduce_add_sync(kFull, cnt) >= keep) t = cand;
+    }
+    __syncwarp();  // every lane has read the buffer before it is rewritten
+    const uint32_t lt = (1u << lane) - 1u;
+    int pos = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const bool take = i * 32 + lane < m && key[i] > t;
+        const uint32_t b = __ballot_sync(kFull, take);
+        if (take) {
+            const int p = pos + __popc(b & lt);
+            s[p] = key2f(key[i]);
+            c[p] = id[i];
+        }
+        pos += __popc(b);
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const bool tie = i * 32 + lane < m && key[i] == t;
+        const uint32_t b = __ballot_sync(kFull, tie);
+        const int p = pos + __popc(b & lt);
+        if (tie && p < keep) {
+            s[p] = key2f(key[i]);
+            c[p] = id[i];
+        }
+        pos += __popc(b);
+    }
+    __syncwarp();
+    return key2f(t);
+}
+
+// Stage one 64-wide K chunk of `rows` rows starting at global row r0 into the
+// core-matrix layout at `dst` (zero fill past nrows and past d); thread `tid`
+// of `nthr` takes every nthr-th 16-byte piece.
+__device__ __forceinline__ void stage_chunk(uint32_t dst, const __nv_bfloat16 *src, int64_t r0, int rows,
+                                            int64_t nrows, int d, int k0, int tid, int nthr) {
+    const int pieces = rows * (kKC / 8);
+    for (int p = tid; p < pieces; p += nthr) {
+        const int row = p >> 3, kg = p & 7;
+        const int64_t gr = r0 + row;
+        const int k = k0 + kg * 8;
+        const bool ok = gr < nrows && k < d;
+        const __nv_bfloat16 *g = ok ? src + gr * d + k : src;
+        const uint32_t off = (uint32_t)(((row >> 3) * 8 + kg) * 128 + (row & 7) * 16);
+        cp_async16(dst + off, g, ok ? 16u : 0u);
+    }
+}
+
+// Warp roles: 0-1 stage operands (cp.async, completion on per-stage "full"
+// barriers), 2 issues the MMAs (lane 0; stage freed through "empty" barriers
+// by tcgen05.commit) and owns TMEM, 3-6 read the two alternating 256-column
+// accumulators (rows 32 * (warp % 4) + lane) while the next tile is computed.
+__global__ void __launch_bounds__(kThreads, 1)
+knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat16 *__restrict__ X,
+              int64_t n, int d, int stages, int C, float *__restrict__ buf_s,
+              uint32_t *__restrict__ buf_i, uint32_t *__restrict__ out_i, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], acc_full[2], acc_empty[2], a_full;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    volatile int *abort_v = &abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nkc = (d + kKC - 1) / kKC;
+    const uint32_t a_base = smem_addr(smem);
+    const uint32_t b_base = a_base + (uint32_t)nkc * kChunkA;
+    const int64_t m0 = (int64_t)blockIdx.x * kTM;
+    const int64_t ntiles = (n + kTN - 1) / kTN;
+    const int64_t nchunks = ntiles * nkc;
+
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full_bar[s], kProducers);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4 * 32);
+        }
+        mbar_init(&a_full, kProducers);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp < 2) {
+        // ---- producers ----
+        for (int c = 0; c < nkc; ++c) stage_chunk(a_base + (uint32_t)c * kChunkA, T, m0, kTM, nt, d, c * kKC, tid, kProducers);
+        cp_async_arrive(&a_full);
+        for (int64_t g = 0; g < nchunks; ++g) {
+            const int s = (int)(g % stages);
+            const uint32_t use = (uint32_t)(g / stages);
+            if (use > 0 && !mbar_wait(&empty_bar[s], (use - 1) & 1, abort_v)) break;
+            const int64_t t = g / nkc;
+            const int c = (int)(g - t * nkc);
+            stage_chunk(b_base + (uint32_t)s * kChunkB, X, t * kTN, kTN, n, d, c * kKC, tid, kProducers);
+            cp_async_arrive(&full_bar[s]);
+        }
+        cp_async_wait<0>();
+    } else if (warp == kMmaWarp) {
+        // ---- MMA issue ----
+        if (lane == 0 && mbar_wait(&a_full, 0, abort_v)) {
+            fence_async_smem();  // cp.async data, written through the generic proxy, to the tensor core
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t t = 0; t < ntiles && ok; ++t) {
+                const int b = (int)(t & 1);
+                const uint32_t ub = (uint32_t)(t >> 1);
+                if (ub > 0 && !mbar_wait(&acc_empty[b], (ub - 1) & 1, abort_v)) break;
+                tc_fence_after();
+                for (int c = 0; c < nkc; ++c, ++g) {
+                    const int s = (int)(g % stages);
+                    if (!mbar_wait(&full_bar[s], (uint32_t)(g / stages) & 1, abort_v)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_async_smem();
+                    tc_fence_after();
+                    const uint32_t a_chunk = a_base + (uint32_t)c * kChunkA;
+                    const uint32_t b_chunk = b_base + (uint32_t)s * kChunkB;
+#pragma unroll
+                    for (int ks = 0; ks < kKC / 16; ++ks) {
+                        const uint64_t ad = smem_desc(a_chunk + ks * 256, 128, 1024);
+                        const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024);
+                        tc_mma(tmem + (uint32_t)(b * kTN), ad, bd, (c > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    tc_commit(&empty_bar[s]);
+                }
+                if (ok) tc_commit(&acc_full[b]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: filter each tile's scores into the row buffers ----
+        // A buffer is cut back to its best C (by the whole warp) between tiles,
+        // once it could not take another full tile; the cut raises the row's
+        // threshold. The accumulator is released before the cuts run.
+        const int q = warp & 3;
+        const int64_t wrow0 = m0 + 32 * q;
+        const int64_t row = wrow0 + lane;
+        const bool row_ok = row < nt;
+        float *rs = buf_s + (row_ok ? row : 0) * (int64_t)kCap;
+        uint32_t *ri = buf_i + (row_ok ? row : 0) * (int64_t)kCap;
+        int cnt = 0;
+        float thr = -__int_as_float(0x7f800000);
+        bool done = true;
+        for (int64_t t = 0; t < ntiles; ++t) {
+            const int b = (int)(t & 1);
+            if (!mbar_wait(&acc_full[b], (uint32_t)(t >> 1) & 1, abort_v)) {
+                done = false;
+                break;
+            }
+            tc_fence_after();
+            const int64_t n0 = t * kTN;
+            const int lim = (int)((n - n0) < kTN ? (n - n0) : kTN);
+#pragma unroll 1
+            for (int cb = 0; cb < kTN; cb += 32) {
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTN + cb), v);
+                if (!row_ok) continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (v[j] > thr && cb + j < lim) {
+                        rs[cnt] = v[j];
+                        ri[cnt] = (uint32_t)(n0 + cb + j);
+                        ++cnt;
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[b]);
+            __syncwarp();
+            uint32_t full = __ballot_sync(kFull, row_ok && cnt > kCap - kTN);
+            while (full) {
+                const int src = __ffs(full) - 1;
+                full &= full - 1;
+                const int m = __shfl_sync(kFull, cnt, src);
+                const float th = warp_cut(buf_s + (wrow0 + src) * kCap, buf_i + (wrow0 + src) * kCap, m, C, lane);
+                if (lane == src) {
+                    thr = th;
+                    cnt = C;
+                }
+            }
+        }
+        if (done && !*abort_v) {
+            __syncwarp();
+            uint32_t over = __ballot_sync(kFull, row_ok && cnt > C);
+            while (over) {
+                const int src = __ffs(over) - 1;
+                over &= over - 1;
+                const int m = __shfl_sync(kFull, cnt, src);
+                warp_cut(buf_s + (wrow0 + src) * kCap, buf_i + (wrow0 + src) * kCap, m, C, lane);
+                if (lane == src) cnt = C;
+            }
+            if (row_ok)
+                for (int j = 0; j < C; ++j) out_i[row * (int64_t)C + j] = j < cnt ? ri[j] : 0xFFFFFFFFu;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_v && tid == 0) atomicExch(err, 1);
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+int knn_tc_stages(int d) {
+    const int nkc = (d + kKC - 1) / kKC;
+    const int budget = 225 * 1024 - nkc * (int)kChunkA;
+    int s = budget / (int)kChunkB;
+    return s > kMaxStages ? kMaxStages : s;
+}
+
+}  // namespace
+
+size_t knn_tc_smem_bytes(int d) {
+    const int nkc = (d + kKC - 1) / kKC;
+    const size_t need = (size_t)nkc * kChunkA + (size_t)knn_tc_stages(d) * kChunkB + 1024;
+    return need < 120 * 1024 ? 120 * 1024 : need;  // one CTA per SM: it holds all 512 TMEM columns
+}
+
+// Candidates (best C per row, unsorted, 0xFFFFFFFF padded) of nt rows of T16
+// against X16 into cand [nt][C]; buf_s/buf_i are [nt][cap] scratch.
+cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloat16 *X16, int64_t n, int d,
+                          int C, int cap, float *buf_s, uint32_t *buf_i, uint32_t *cand, int *err,
+                          cudaStream_t s) {
+    const int stages = knn_tc_stages(d);
+    // A cut must leave room for a whole tile: C + kTN <= kCap.
+    if (stages < 2 || cap != kCap || C < 1 || C + kTN > kCap) return cudaErrorInvalidValue;
+    const size_t smem = knn_tc_smem_bytes(d);
+    cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (nt + kTM - 1) / kTM;
+    knn_tc_kernel<<<(unsigned)blocks, kThreads, smem, s>>>(T16, nt, X16, n, d, stages, C, buf_s, buf_i,
+                                                           cand, err);
+    return cudaGetLastError();
+}
+
+}  // namespace roar

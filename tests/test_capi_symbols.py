@@ -33,7 +33,7 @@ def test_header_declares_the_search_boundary():
 
 
 def test_every_declared_symbol_is_exported(libpath):
-    lib = ctypes.CDLL(libpath)
+    lib = ctypes.CDLL(libpath, mode=os.RTLD_NOW)   # also fails on any unresolved symbol
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
 
