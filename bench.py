@@ -26,7 +26,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-L_SWEEP = [10, 20, 30, 50, 75, 100, 150, 200, 300, 400, 500, 600, 700, 800, 1024]
+L_SWEEP = [10, 20, 30, 40, 50, 60, 70, 80, 90, 100, 110, 120, 150, 200, 300, 400, 500, 700, 1024]
 TARGET_RECALL = 0.90
 METRIC = "QPS at recall@10=0.90 (plain FP32 vs BF16/FP8+rerank); serving p50/p99 ms"
 CACHE_DIR = os.environ.get("ROAR_BENCH_CACHE", "/tmp/roar_bench_cache")

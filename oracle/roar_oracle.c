@@ -29,7 +29,7 @@
  *     is re-pruned with Alg. 3.
  *   - Alg. 3: "for all p in Res" with a strict "<"; fill is on during the
  *     projection and off during connectivity enhancement.
- *   - Alg. 1 lines 9-14: each base row is searched over the projected graph
+ *   - Alg. 1, enhancement loop: each base row is searched over the projected graph
  *     G_pj (fixed during the pass); results are pruned without fill into G';
  *     the final list is N_pj(x) followed by N'(x) minus N_pj(x) (<= 2M).
  *   - reachability repair (not in the paper's algorithm, which claims
@@ -506,7 +506,7 @@ int32_t orc_acquire_neighbors(const float *X, int64_t n, int32_t d, uint32_t x, 
     return r;
 }
 
-/* Reverse-edge update of Alg. 2 line 9 / Alg. 1 line 12: give p the edge
+/* Reverse-edge update of Alg. 2 and of Alg. 1's enhancement loop: give p the edge
  * p -> x. Skip when present; append when there is room; otherwise re-prune
  * N(p) U {x} with Alg. 3. */
 static int reverse_update(const float *X, int32_t d, ulist *G, uint32_t p, uint32_t x, int32_t M,
@@ -534,7 +534,7 @@ static int reverse_update(const float *X, int32_t d, ulist *G, uint32_t p, uint3
 }
 
 /* FP64 beam search over adjacency lists G (used by connectivity enhancement,
- * Alg. 1 line 10). Same algorithm as search_one with FP64 distances and no
+ * the enhancement loop of Alg. 1). Same algorithm as search_one with FP64 distances and no
  * visit cap. Writes the final pool (sorted, size returned). */
 static int32_t beam_search_f64_lists(const float *X, int64_t n, int32_t d, const ulist *G,
                                      uint32_t entry, const float *q, int32_t L, ent64 *pool,
@@ -639,7 +639,7 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
         for (int32_t r = 0; r < nqd; ++r)
             if ((int64_t)knn[t * nqd + r] >= n) { rc = ORC_EINVAL; goto done; }
 
-    /* Alg. 1 lines 2-6: x = the closest base node of t gets the edge x -> t;
+    /* Alg. 1, bipartite step: x = the closest base node of t gets the edge x -> t;
      * N_out(t) keeps the other nqd - 1 ids (knn row from rank 1 on). */
     for (int64_t t = 0; t < nt; ++t)
         if (ul_push(&B[knn[t * nqd]], (uint32_t)t)) goto done;
@@ -684,7 +684,7 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
         free(hasin);
     }
 
-    /* Alg. 1 lines 8-13: connectivity enhancement on G' (a copy of G_pj). */
+    /* Alg. 1, enhancement loop: connectivity enhancement on G' (a copy of G_pj). */
     for (int64_t v = 0; v < n; ++v)
         for (int32_t j = 0; j < Gpj[v].n; ++j)
             if (ul_push(&Gp[v], Gpj[v].v[j])) goto done;
@@ -710,7 +710,7 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
     }
     free(pool);
 
-    /* Alg. 1 line 14: N_pj(x) followed by N'(x) minus N_pj(x). */
+    /* Alg. 1, final union: N_pj(x) followed by N'(x) minus N_pj(x). */
     for (int64_t v = 0; v < n; ++v) {
         for (int32_t j = 0; j < Gpj[v].n; ++j)
             if (ul_push(&F[v], Gpj[v].v[j])) goto done;

@@ -6,14 +6,19 @@
 // run here on host threads, in a batched form that is deterministic for any
 // thread count:
 //   projection:  every pivot's list N'(x) = AcquireNeighbors(x, C(x), M, fill)
-//                is computed independently (Alg. 2 lines 3-7); then every node
+//                is computed independently (Alg. 2, pivot selection); then every node
 //                p receives the reverse edges p -> x of all pivots x with
 //                p in N'(x) at once, re-pruned with Alg. 3 (fill) when the
-//                list would exceed M (Alg. 2 line 9);
-//   enhancement: every node's supplementary list is AcquireNeighbors over its
-//                beam-search result without fill (Alg. 1 lines 10-11), then
-//                reverse edges are added the same batched way (line 12) and
-//                the lists are merged with the projected graph (line 14);
+//                list would exceed M (Alg. 2, reverse-edge step);
+//   enhancement: the rows are taken in chunks of doubling size; every row's
+//                supplementary list is AcquireNeighbors over its beam-search
+//                result without fill (Alg. 1, enhancement loop), then the chunk's
+//                reverse edges are added the same batched way, and
+//                the next chunk searches G_pj merged with all supplementary
+//                edges so far (Alg. 1's final union, formed early): on data whose
+//                clusters G_pj leaves unconnected, the reverse edges of the
+//                first rows are what lets later searches leave the medoid's
+//                cluster;
 //   repair:      any node the final graph cannot reach from the entry gets an
 //                edge from the nearest reachable node the search finds.
 // The sequential order of the paper's loops (each pivot seeing the reverse
@@ -121,41 +126,47 @@ struct Lists {
     const uint32_t *row(int64_t i) const { return v.data() + (size_t)i * cap; }
 };
 
-// Batched reverse-edge round (Alg. 2 line 9 / Alg. 1 line 12): every node p
-// gets p -> x for all x with p in fwd(x); lists over M are re-pruned with
-// Alg. 3. Without fill, the free slots left by the pruning are topped up with
-// the remaining reverse edges, nearest first: the paper's sequential loop
-// appends a reverse edge whenever the list has room, so its lists end up full
-// of reverse edges after each pruning, and the top-up gives the batched round
-// the same outcome.
+// Batched reverse-edge round (Alg. 2 and Alg. 1's enhancement loop) for the
+// forward edges of the sources x in [s0, s1): every node p gets p -> x for all
+// such x with p in fwd(x); lists over M are re-pruned with Alg. 3. Without
+// fill, the free slots left by the pruning are topped up with the remaining
+// reverse edges, nearest first: the paper's sequential loop appends a reverse
+// edge whenever the list has room, so its lists end up full of reverse edges
+// after each pruning, and the top-up gives the batched round the same outcome.
 // A node that many lists point to (a hub) keeps at most `max_in` of its
-// reverse-edge candidates, the nearest ones, before pruning.
-void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lists &fwd, int max_in) {
+// reverse-edge candidates, the nearest ones, before pruning. Lists are
+// updated in place; nodes without incoming edges keep theirs. Every changed
+// node is flagged in `dirty` when it is given.
+void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lists &fwd, int max_in,
+                       int64_t s0, int64_t s1, std::vector<unsigned char> *dirty = nullptr) {
     const int64_t n = fwd.n;
     std::vector<int64_t> off((size_t)n + 1, 0);
-    for (int64_t x = 0; x < n; ++x)
+    for (int64_t x = s0; x < s1; ++x)
         for (int j = 0; j < fwd.cnt[x]; ++j) ++off[fwd.row(x)[j] + 1];
     for (int64_t i = 0; i < n; ++i) off[i + 1] += off[i];
     std::vector<uint32_t> inc((size_t)off[n]);
     std::vector<int64_t> fillpos(off.begin(), off.end() - 1);
-    for (int64_t x = 0; x < n; ++x)  // ascending x: deterministic incoming order
+    for (int64_t x = s0; x < s1; ++x)  // ascending x: deterministic incoming order
         for (int j = 0; j < fwd.cnt[x]; ++j) inc[fillpos[fwd.row(x)[j]]++] = (uint32_t)x;
-    Lists out;
-    out.init(n, M);
+    fillpos.clear();
+    fillpos.shrink_to_fit();
     parallel_for(n, threads, [&](int64_t p, int) {
-        const uint32_t *f = fwd.row(p);
+        if (off[p] == off[p + 1]) return;
+        if (dirty) (*dirty)[p] = 1;
         const int nf = fwd.cnt[p];
-        std::vector<uint32_t> all(f, f + nf);
+        std::vector<uint32_t> all(fwd.row(p), fwd.row(p) + nf);  // own list first
+        const uint32_t *f = all.data();
         // Incoming ids are distinct and ascending; only the own list can repeat them.
         for (int64_t k = off[p]; k < off[p + 1]; ++k) {
             const uint32_t x = inc[k];
             if (x == (uint32_t)p) continue;
             if (std::find(f, f + nf, x) == f + nf) all.push_back(x);
+            f = all.data();
         }
-        uint32_t *o = out.row(p);
+        uint32_t *o = fwd.row(p);
         if ((int)all.size() <= M) {
             std::copy(all.begin(), all.end(), o);
-            out.cnt[p] = (int)all.size();
+            fwd.cnt[p] = (int)all.size();
             return;
         }
         std::vector<Cand> C;
@@ -178,9 +189,23 @@ void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lis
                 o[r++] = c;
             }
         }
-        out.cnt[p] = r;
+        fwd.cnt[p] = r;
     });
-    fwd = std::move(out);
+}
+
+// Row x of the searched / final graph: N_pj(x) followed by the supplementary
+// edges not already in it (Alg. 1's final union); returns the row's length.
+int merge_row(const Lists &pj, const Lists &ce, int64_t x, uint32_t *row, int R) {
+    int k = 0;
+    for (int j = 0; j < pj.cnt[x]; ++j) row[k++] = pj.row(x)[j];
+    for (int j = 0; j < ce.cnt[x]; ++j) {
+        const uint32_t u = ce.row(x)[j];
+        bool dup = false;
+        for (int t = 0; t < pj.cnt[x]; ++t) dup |= pj.row(x)[t] == u;
+        if (!dup) row[k++] = u;
+    }
+    for (int j = k; j < R; ++j) row[j] = kNone;
+    return k;
 }
 
 double seconds_since(std::chrono::steady_clock::time_point t0) {
@@ -320,7 +345,7 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
     st[1] = seconds_since(t0);
     build_log("kNN of %.0f training queries done in %.1f s", (double)nt, st[1]);
 
-    // Alg. 1 lines 2-6: base node x = 1-NN(t) gets the edge x -> t.
+    // Alg. 1, bipartite step: base node x = 1-NN(t) gets the edge x -> t.
     t0 = std::chrono::steady_clock::now();
     std::vector<int64_t> boff((size_t)n + 1, 0);
     for (int64_t t = 0; t < nt; ++t) ++boff[knn[(size_t)t * nq_depth] + 1];
@@ -330,7 +355,7 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         std::vector<int64_t> pos(boff.begin(), boff.end() - 1);
         for (int64_t t = 0; t < nt; ++t) bq[pos[knn[(size_t)t * nq_depth]]++] = (uint32_t)t;
     }
-    // Alg. 2 lines 2-7: each pivot selects from its bridges' other neighbours.
+    // Alg. 2, pivot selection: each pivot selects from its bridges' other neighbours.
     Lists pj;
     pj.init(n, M);
     std::atomic<int64_t> pivots{0};
@@ -356,8 +381,8 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         std::sort(C.begin(), C.end(), cand_less);
         pj.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, true, pj.row(x));
     });
-    // Alg. 2 line 9, batched.
-    add_reverse_edges(X.data(), d, M, true, threads, pj, 4 * L_build);
+    // Alg. 2, reverse-edge step, batched.
+    add_reverse_edges(X.data(), d, M, true, threads, pj, 4 * L_build, 0, n);
     // The enhancement searches start at the medoid and walk G_pj: a medoid
     // that no pivot selected has no edges there and every search would stop
     // at once. Such a medoid gets a list as a pivot would, from its own
@@ -390,27 +415,43 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
     int64_t pj_edges = 0;
     for (int64_t i = 0; i < n; ++i) pj_edges += pj.cnt[i];
 
-    // Alg. 1 lines 9-11: beam search of every base row over G_pj (GPU), then
-    // AcquireNeighbors without fill.
+    // Alg. 1, enhancement loop: beam search of every base row (GPU), AcquireNeighbors
+    // without fill, reverse edges. The rows are processed in chunks of
+    // doubling size (1024, 1024, 2048, ... up to n / 32, at least 131072 and
+    // at most 524288), and each chunk
+    // searches G_pj merged with the supplementary edges of the chunks before
+    // it: a reverse edge p -> x added for an earlier row gives later searches
+    // a route from the medoid's region to x's, which G_pj alone may lack (on
+    // well separated clusters it has no edge between them). A row's own list
+    // is pruned from its search result together with the reverse edges it has
+    // already received.
     t0 = std::chrono::steady_clock::now();
     Lists ce;
     ce.init(n, M);
+    std::vector<uint32_t> adj((size_t)n * R, kNone);
+    std::vector<int> deg((size_t)n, 0);
+    std::vector<unsigned char> dirty((size_t)n, 1);  // rows whose merged form is stale
     {
-        uint32_t *pj_dev = nullptr, *pid = nullptr;
+        uint32_t *pid = nullptr;
         float *pdist = nullptr;
-        const int64_t chunk = std::min<int64_t>(n, 131072);
-        e = cudaMalloc(&pj_dev, (size_t)n * M * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&pid, (size_t)chunk * L_build * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&pdist, (size_t)chunk * L_build * 4);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(pj_dev, pj.v.data(), (size_t)n * M * 4, cudaMemcpyHostToDevice, s);
+        const int64_t max_chunk = std::min<int64_t>(n, std::min<int64_t>(524288, std::max<int64_t>(131072, n / 32)));
+        e = cudaMalloc(&pid, (size_t)max_chunk * L_build * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&pdist, (size_t)max_chunk * L_build * 4);
         roar_index *gi = nullptr;
         if (e == cudaSuccess)
-            rc = roar_index_create(n, d, X_dev, ROAR_F32, nullptr, nullptr, pj_dev, M, entry, 32768, &gi);
-        std::vector<uint32_t> hid((size_t)chunk * L_build);
-        std::vector<float> hd((size_t)chunk * L_build);
-        for (int64_t q0 = 0; e == cudaSuccess && rc == ROAR_OK && q0 < n; q0 += chunk) {
-            const int64_t qn = std::min(chunk, n - q0);
+            rc = roar_index_create(n, d, X_dev, ROAR_F32, nullptr, nullptr, adj_dev, R, entry, 32768, &gi);
+        std::vector<uint32_t> hid((size_t)max_chunk * L_build);
+        std::vector<float> hd((size_t)max_chunk * L_build);
+        int64_t q0 = 0;
+        while (e == cudaSuccess && rc == ROAR_OK && q0 < n) {
+            const int64_t qn = std::min(n - q0, std::min(max_chunk, std::max<int64_t>(1024, q0)));
+            parallel_for(n, threads, [&](int64_t x, int) {
+                if (!dirty[x]) return;
+                dirty[x] = 0;
+                deg[x] = merge_row(pj, ce, x, adj.data() + (size_t)x * R, R);
+            });
+            e = cudaMemcpyAsync(adj_dev, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) break;
             rc = roar_search(gi, X_dev + (size_t)q0 * d, qn, L_build, L_build, pid, pdist, nullptr,
                              nullptr, nullptr, stream);
             if (rc != ROAR_OK) break;
@@ -419,47 +460,45 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
                 e = cudaMemcpyAsync(hd.data(), pdist, (size_t)qn * L_build * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) break;
-            build_log("enhancement: searched %.0f of %.0f rows (%.1f s)", (double)(q0 + qn), (double)n,
-                      seconds_since(t0));
             parallel_for(qn, threads, [&](int64_t i, int) {
                 const int64_t x = q0 + i;
                 std::vector<Cand> C;
-                C.reserve((size_t)L_build);
+                C.reserve((size_t)L_build + M);
                 for (int j = 0; j < L_build; ++j) {
                     const uint32_t u = hid[(size_t)i * L_build + j];
                     if (u == kNone || u == (uint32_t)x) continue;
                     C.emplace_back(hd[(size_t)i * L_build + j], u);
                 }
+                const float *xv = X.data() + (size_t)x * d;
+                for (int j = 0; j < ce.cnt[x]; ++j) {  // reverse edges received so far
+                    const uint32_t u = ce.row(x)[j];
+                    bool dup = false;
+                    for (const Cand &c : C) dup |= c.second == u;
+                    if (!dup) C.emplace_back(neg_dot(xv, X.data() + (size_t)u * d, d), u);
+                }
+                std::sort(C.begin(), C.end(), cand_less);
                 ce.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, false, ce.row(x));
+                dirty[x] = 1;
             });
+            add_reverse_edges(X.data(), d, M, false, threads, ce, 4 * L_build, q0, q0 + qn, &dirty);
+            q0 += qn;
+            build_log("enhancement: searched %.0f of %.0f rows (%.1f s)", (double)q0, (double)n,
+                      seconds_since(t0));
         }
         roar_index_destroy(gi);
-        cudaFree(pj_dev);
         cudaFree(pid);
         cudaFree(pdist);
         if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: enhancement search");
         if (rc != ROAR_OK) return rc;
     }
     st[3] = seconds_since(t0);
-    // Alg. 1 line 12 (batched, no fill), then line 14: N_pj followed by the new edges.
+    // Alg. 1, final union: N_pj followed by the new edges.
     t0 = std::chrono::steady_clock::now();
-    add_reverse_edges(X.data(), d, M, false, threads, ce, 4 * L_build);
-    std::vector<uint32_t> adj((size_t)n * R, kNone);
-    std::vector<int> deg((size_t)n, 0);
     parallel_for(n, threads, [&](int64_t x, int) {
-        uint32_t *row = adj.data() + (size_t)x * R;
-        int k = 0;
-        for (int j = 0; j < pj.cnt[x]; ++j) row[k++] = pj.row(x)[j];
-        for (int j = 0; j < ce.cnt[x]; ++j) {
-            const uint32_t u = ce.row(x)[j];
-            bool dup = false;
-            for (int t = 0; t < pj.cnt[x]; ++t) dup |= pj.row(x)[t] == u;
-            if (!dup) row[k++] = u;
-        }
-        deg[x] = k;
+        if (dirty[x]) deg[x] = merge_row(pj, ce, x, adj.data() + (size_t)x * R, R);
     });
     st[4] = seconds_since(t0);
-    build_log("enhancement done: search+prune %.1f s, reverse+merge %.1f s", st[3], st[4]);
+    build_log("enhancement done: search+prune %.1f s, merge %.1f s", st[3], st[4]);
 
     // Reachability repair: each unreachable node gets an edge from the
     // nearest node (among the 16 the search finds from the entry) that still

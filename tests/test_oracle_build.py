@@ -44,7 +44,7 @@ def test_every_node_reachable_from_entry(tiny):
 
 def test_projection_edges_come_from_bipartite_candidates(tiny):
     """Every G_pj edge a->b links a pivot to a node reached through one of
-    its bridge queries (Alg. 2 lines 3-5), either forward (b in U(a)) or as
+    its bridge queries (Alg. 2's candidate collection), either forward (b in U(a)) or as
     the reverse edge of a pivot b (a in U(b))."""
     knn = tiny["knn"]
     n = tiny["X"].shape[0]
