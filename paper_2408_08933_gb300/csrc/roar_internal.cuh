@@ -18,6 +18,19 @@ constexpr int kMaxWarpsPerSm = 32;
 #define ROAR_MIN_BLOCKS 5
 #endif
 constexpr int kMinBlocksPerSm = ROAR_MIN_BLOCKS;  // register budget: 65536 / (blocks * 128)
+// The BF16 / FP8 traversal kernels hold narrower row chunks and are compiled
+// for more resident CTAs: measured on GB300 (1M x 200, L = 20-300), 6 CTAs per
+// SM for BF16 and 8 for FP8 were fastest despite a few hundred bytes of spills.
+#ifndef ROAR_MIN_BLOCKS_BF16
+#define ROAR_MIN_BLOCKS_BF16 6
+#endif
+#ifndef ROAR_MIN_BLOCKS_FP8
+#define ROAR_MIN_BLOCKS_FP8 8
+#endif
+template <int DT>
+__host__ __device__ constexpr int min_blocks_per_sm() {
+    return DT == 0 ? ROAR_MIN_BLOCKS : (DT == 1 ? ROAR_MIN_BLOCKS_BF16 : ROAR_MIN_BLOCKS_FP8);
+}
 #define ROAR_NOALLOC_SCRATCH_BYTES (64ull << 20)
 
 // Everything one search launch needs. Plain pointers: the launch reads the

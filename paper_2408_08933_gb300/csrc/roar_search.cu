@@ -29,9 +29,10 @@ const void *search_kernel(int dtype, int d, int rmax, int tw) {
 }
 
 int hash_log2_for(int L) {
-    // Measured on GB300 (1M x 200, 10k queries): the shared table wins for
-    // short searches, the bitmap alone (more resident warps) from L ~ 100 on.
-    if (L >= 96) return 0;
+    // Measured on GB300 (1M x 200, 10k queries, FP32 / BF16 / FP8): the
+    // global bitmap alone is faster from L = 20 on (15-20 % at L = 60-90); the
+    // shared table only helps the shortest searches.
+    if (L >= 16) return 0;
     const int lcap = (L + 31) / 32 * 32;
     const size_t budget = (size_t)(228 - kMinBlocksPerSm) * 1024;  // per SM, minus per-CTA reserve
     int lg = 10;

@@ -106,13 +106,17 @@ __device__ __forceinline__ float4 to_f4(const RawChunk<DT> &r) {
     }
 }
 
-// Rows gathered per batch: about ROAR_BATCH_CHUNKS 16-byte loads in flight per lane.
+// Rows gathered per batch: FP32 rows about ROAR_BATCH_CHUNKS 16-byte loads in
+// flight per lane; BF16 / FP8 chunks are 8 / 4 bytes, so twice as many rows
+// (at most 8) fit the same registers and halve the gather round trips per hop.
 #ifndef ROAR_BATCH_CHUNKS
 #define ROAR_BATCH_CHUNKS 8
 #endif
-template <int NCH>
+template <int DT, int NCH>
 __host__ __device__ constexpr int batch_rows() {
-    return NCH >= ROAR_BATCH_CHUNKS ? 1 : ROAR_BATCH_CHUNKS / NCH;
+    constexpr int f32 = NCH >= ROAR_BATCH_CHUNKS ? 1 : ROAR_BATCH_CHUNKS / NCH;
+    constexpr int lowp = 2 * f32 > 8 ? (f32 > 8 ? f32 : 8) : 2 * f32;
+    return DT == 0 ? f32 : lowp;
 }
 
 // Distances for rows ids_s[j] (shared, expanded bit ignored), j = first,
@@ -124,6 +128,10 @@ __device__ __forceinline__ void score_rows(const void *base, const float *scales
                                            float *out_s, int lane, int first = 0, int step = B) {
     for (int j0 = first; j0 < cnt; j0 += step) {
         RawChunk<DT> raw[B][NCH];
+        float sc = 1.0f;  // FP8: lane b < B holds row j0 + b's scale, loaded with the rows
+        if constexpr (DT == 2) {
+            if (scales && lane < B && j0 + lane < cnt) sc = __ldg(scales + (ids_s[j0 + lane] & kIdMask));
+        }
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int j = j0 + b;
@@ -162,7 +170,6 @@ __device__ __forceinline__ void score_rows(const void *base, const float *scales
         __syncwarp();
         if (lane < B && j0 + lane < cnt) {
             if constexpr (DT == 2) {
-                const float sc = scales ? __ldg(scales + (ids_s[j0 + lane] & kIdMask)) : 1.0f;
                 out_s[j0 + lane] = -(sc * mine);
             } else {
                 out_s[j0 + lane] = -mine;
@@ -265,13 +272,14 @@ __device__ __forceinline__ int lower_bound_entries(const float *dv, const uint32
 }
 
 
-// Launch shape of a team of TW warps per query: CTAs of max(4, TW) warps.
-template <int TW>
+// Launch shape of a team of TW warps per query: CTAs of max(4, TW) warps,
+// with the register budget of min_blocks_per_sm<DT>() 4-warp CTAs per SM.
+template <int DT, int TW>
 struct TeamShape {
     static constexpr int kThreads = 32 * (TW > kWarpsPerBlock ? TW : kWarpsPerBlock);
     static constexpr int kTeams = kThreads / (32 * TW);
-    static constexpr int kMinBlocks =
-        (kMinBlocksPerSm * 32 * kWarpsPerBlock) / kThreads > 0 ? (kMinBlocksPerSm * 32 * kWarpsPerBlock) / kThreads : 1;
+    static constexpr int kWarpBudget = min_blocks_per_sm<DT>() * kWarpsPerBlock;
+    static constexpr int kMinBlocks = (kWarpBudget * 32) / kThreads > 0 ? (kWarpBudget * 32) / kThreads : 1;
 };
 
 // One query per team of TW warps. The leader warp (warp 0 of the team)
@@ -281,12 +289,13 @@ struct TeamShape {
 // RPL = adjacency ids per lane (rmax <= 32 * RPL), which also bounds the new
 // candidates of one hop.
 template <int DT, int NCH, int RPL, int TW>
-__global__ void __launch_bounds__(TeamShape<TW>::kThreads, TeamShape<TW>::kMinBlocks)
+__global__ void __launch_bounds__(TeamShape<DT, TW>::kThreads, TeamShape<DT, TW>::kMinBlocks)
 beam_search_kernel(const SearchArgs a) {
     constexpr int kMaxRowPerLane = RPL;
     constexpr int kMaxCandPerLane = RPL;
-    constexpr int TPB = TeamShape<TW>::kTeams;
-    constexpr int B = batch_rows<NCH>();
+    constexpr int TPB = TeamShape<DT, TW>::kTeams;
+    constexpr int B = batch_rows<DT, NCH>();   // traversal rows per batch
+    constexpr int B0 = batch_rows<0, NCH>();   // FP32 re-rank rows per batch
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -596,7 +605,7 @@ beam_search_kernel(const SearchArgs a) {
         // Output (re-ranked in FP32, in place, for the reduced-precision forms).
         const int fsize = ctl[2];
         if constexpr (DT != 0) {
-            score_rows<0, NCH, B>(a.base32, nullptr, d, d4, qr, pi, fsize, pd, lane, wt * B, TW * B);
+            score_rows<0, NCH, B0>(a.base32, nullptr, d, d4, qr, pi, fsize, pd, lane, wt * B0, TW * B0);
             tsync();
             if (leader) {
                 for (int i = lane; i < fsize; i += 32) {

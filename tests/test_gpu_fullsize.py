@@ -41,10 +41,10 @@ def _search(idx, Qd, k, L):
 SAMPLE = np.random.default_rng(5).choice(10_000, 12, replace=False)
 
 
-@pytest.mark.parametrize("L,tw", [(1024, 1), (100, 1), (100, 4)])
-def test_fp32_full_batch_sampled_parity(full, L, tw):
+@pytest.mark.parametrize("L,tw,hash_log2", [(1024, 1, -1), (100, 1, -1), (100, 4, -1), (90, 1, 0), (90, 1, 10)])
+def test_fp32_full_batch_sampled_parity(full, L, tw, hash_log2):
     idx = dev_index(full["X"], full["adj"], full["entry"], max_visits=MV)
-    idx.set_tuning(L, tw, -1 if L >= 96 else 0, 0)     # the bench's tuned launch shape
+    idx.set_tuning(L, tw, hash_log2, 0)     # bench-like launch shapes: bitmap, auto, shared table
     got = _search(idx, _device(full["Q"]), 10, L)     # the whole 10k batch in one launch
     idx.close()
     Qs = full["Q"][SAMPLE]
