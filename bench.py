@@ -518,7 +518,9 @@ def main():
     achieved = bytes_q * nq / (avg_ms / 1e3) / 1e9
     peak, peak_src = _peaks()
     src_hash = _src_hash(["paper_2408_08933_gb300/csrc/roar_search_kernel.cuh",
-                          "paper_2408_08933_gb300/csrc/roar_search.cu"])
+                          "paper_2408_08933_gb300/csrc/roar_search.cu",
+                          "paper_2408_08933_gb300/csrc/roar_internal.cuh",
+                          "paper_2408_08933_gb300/csrc/roar_search_f32.cu"])
     traffic = _traffic(f"search_f32_{w.name}.txt", src_hash)
 
     # ---- e2e: host buffers through roar_search_host -----------------------------

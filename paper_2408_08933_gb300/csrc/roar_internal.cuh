@@ -15,7 +15,7 @@ constexpr int kWarpsPerBlock = 4;            // one query per warp, 4 per CTA
 constexpr int kCandCap = ROAR_MAX_RMAX;      // new neighbours per hop, at most rmax
 constexpr int kMaxWarpsPerSm = 32;
 #ifndef ROAR_MIN_BLOCKS
-#define ROAR_MIN_BLOCKS 5
+#define ROAR_MIN_BLOCKS 4
 #endif
 constexpr int kMinBlocksPerSm = ROAR_MIN_BLOCKS;  // register budget: 65536 / (blocks * 128)
 // The BF16 / FP8 traversal kernels hold narrower row chunks and are compiled

@@ -107,15 +107,28 @@ __device__ __forceinline__ float4 to_f4(const RawChunk<DT> &r) {
 }
 
 // Rows gathered per batch: FP32 rows about ROAR_BATCH_CHUNKS 16-byte loads in
-// flight per lane; BF16 / FP8 chunks are 8 / 4 bytes, so twice as many rows
-// (at most 8) fit the same registers and halve the gather round trips per hop.
+// flight per lane (measured on GB300: 12 with 4 CTAs per SM beat 8 with 5, and
+// every deeper or shallower pairing); BF16 / FP8 chunks are 8 / 4 bytes, so
+// twice as many rows (at most ROAR_LOWP_MAX_ROWS) fit the same registers.
 #ifndef ROAR_BATCH_CHUNKS
-#define ROAR_BATCH_CHUNKS 8
+#define ROAR_BATCH_CHUNKS 12
 #endif
+#ifndef ROAR_LOWP_MAX_ROWS
+#define ROAR_LOWP_MAX_ROWS 8
+#endif
+// The FP32 re-rank inside the BF16 / FP8 kernels gathers fewer rows per batch
+// (ROAR_RERANK_CHUNKS loads per lane): those kernels run with fewer registers.
+#ifndef ROAR_RERANK_CHUNKS
+#define ROAR_RERANK_CHUNKS 8
+#endif
+template <int NCH>
+__host__ __device__ constexpr int rerank_rows() {
+    return NCH >= ROAR_RERANK_CHUNKS ? 1 : ROAR_RERANK_CHUNKS / NCH;
+}
 template <int DT, int NCH>
 __host__ __device__ constexpr int batch_rows() {
     constexpr int f32 = NCH >= ROAR_BATCH_CHUNKS ? 1 : ROAR_BATCH_CHUNKS / NCH;
-    constexpr int lowp = 2 * f32 > 8 ? (f32 > 8 ? f32 : 8) : 2 * f32;
+    constexpr int lowp = 2 * f32 > ROAR_LOWP_MAX_ROWS ? (f32 > ROAR_LOWP_MAX_ROWS ? f32 : ROAR_LOWP_MAX_ROWS) : 2 * f32;
     return DT == 0 ? f32 : lowp;
 }
 
@@ -295,7 +308,7 @@ beam_search_kernel(const SearchArgs a) {
     constexpr int kMaxCandPerLane = RPL;
     constexpr int TPB = TeamShape<DT, TW>::kTeams;
     constexpr int B = batch_rows<DT, NCH>();   // traversal rows per batch
-    constexpr int B0 = batch_rows<0, NCH>();   // FP32 re-rank rows per batch
+    constexpr int B0 = rerank_rows<NCH>();     // FP32 re-rank rows per batch (BF16 / FP8 only)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
