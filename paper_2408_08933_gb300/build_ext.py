@@ -17,7 +17,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUFLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE,
                   "-I", CSRC] + os.environ.get("ROAR_NVCC_FLAGS", "").split()
-CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", CSRC,
+CXXFLAGS = ["-O3", "-ffp-contract=off", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", CSRC,
             "-I", "/usr/local/cuda/include"]
 LDLIBS = ["-lpthread"]
 

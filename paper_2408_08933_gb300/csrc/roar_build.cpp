@@ -208,6 +208,21 @@ int merge_row(const Lists &pj, const Lists &ce, int64_t x, uint32_t *row, int R)
     return k;
 }
 
+// Page-locks an existing host buffer for the lifetime of the guard (faster
+// repeated uploads); if the driver refuses, the buffer stays pageable.
+struct HostPin {
+    void *p = nullptr;
+    HostPin(void *ptr, size_t bytes) {
+        if (cudaHostRegister(ptr, bytes, cudaHostRegisterDefault) == cudaSuccess) p = ptr;
+        else cudaGetLastError();
+    }
+    ~HostPin() {
+        if (p) cudaHostUnregister(p);
+    }
+    HostPin(const HostPin &) = delete;
+    HostPin &operator=(const HostPin &) = delete;
+};
+
 double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -429,8 +444,10 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
     Lists ce;
     ce.init(n, M);
     std::vector<uint32_t> adj((size_t)n * R, kNone);
+    HostPin adj_pin(adj.data(), adj.size() * 4);      // uploaded once per chunk
     std::vector<int> deg((size_t)n, 0);
     std::vector<unsigned char> dirty((size_t)n, 1);  // rows whose merged form is stale
+    double t_merge = 0, t_search = 0, t_prune = 0, t_rev = 0;
     {
         uint32_t *pid = nullptr;
         float *pdist = nullptr;
@@ -445,6 +462,7 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         int64_t q0 = 0;
         while (e == cudaSuccess && rc == ROAR_OK && q0 < n) {
             const int64_t qn = std::min(n - q0, std::min(max_chunk, std::max<int64_t>(1024, q0)));
+            auto tp = std::chrono::steady_clock::now();
             parallel_for(n, threads, [&](int64_t x, int) {
                 if (!dirty[x]) return;
                 dirty[x] = 0;
@@ -452,6 +470,8 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
             });
             e = cudaMemcpyAsync(adj_dev, adj.data(), adj.size() * 4, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) break;
+            t_merge += seconds_since(tp);
+            tp = std::chrono::steady_clock::now();
             rc = roar_search(gi, X_dev + (size_t)q0 * d, qn, L_build, L_build, pid, pdist, nullptr,
                              nullptr, nullptr, stream);
             if (rc != ROAR_OK) break;
@@ -460,6 +480,8 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
                 e = cudaMemcpyAsync(hd.data(), pdist, (size_t)qn * L_build * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) break;
+            t_search += seconds_since(tp);
+            tp = std::chrono::steady_clock::now();
             parallel_for(qn, threads, [&](int64_t i, int) {
                 const int64_t x = q0 + i;
                 std::vector<Cand> C;
@@ -480,7 +502,10 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
                 ce.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, false, ce.row(x));
                 dirty[x] = 1;
             });
+            t_prune += seconds_since(tp);
+            tp = std::chrono::steady_clock::now();
             add_reverse_edges(X.data(), d, M, false, threads, ce, 4 * L_build, q0, q0 + qn, &dirty);
+            t_rev += seconds_since(tp);
             q0 += qn;
             build_log("enhancement: searched %.0f of %.0f rows (%.1f s)", (double)q0, (double)n,
                       seconds_since(t0));
@@ -499,6 +524,8 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
     });
     st[4] = seconds_since(t0);
     build_log("enhancement done: search+prune %.1f s, merge %.1f s", st[3], st[4]);
+    build_log("enhancement split: merge+upload %.1f s, GPU search %.1f s, prune %.1f s", t_merge, t_search, t_prune);
+    build_log("enhancement split: reverse edges %.1f s", t_rev);
 
     // Reachability repair: each unreachable node gets an edge from the
     // nearest node (among the 16 the search finds from the entry) that still
