@@ -82,9 +82,33 @@ __host__ __device__ inline size_t search_smem_per_warp(int lcap, int hash_log2) 
     return (size_t)lcap * 8 + (size_t)kCandCap * 16 + (hash_log2 ? ((size_t)4 << hash_log2) : 0);
 }
 
-// Per team: the above plus a 16-byte control block (claimed query, hop count, pool size).
-__host__ __device__ inline size_t search_smem_per_team(int lcap, int hash_log2) {
-    return search_smem_per_warp(lcap, hash_log2) + 16;
+// 16-byte row chunks a lane holds: rows of d floats are d/4 chunks dealt to
+// 32 lanes, NCH = 1, 2, 4 or 8 per lane.
+__host__ __device__ inline int search_nch(int d) {
+    const int need = ((d >> 2) + 31) / 32;
+    return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
+}
+
+// The FP32 one-warp kernel stages its row gathers in shared memory: two
+// buffers of stage_rows(NCH) rows per warp (ROAR_STAGE_ROWS rows for d <= 256,
+// proportionally fewer for wider rows; 0 turns staging off).
+#ifndef ROAR_STAGE_ROWS
+#define ROAR_STAGE_ROWS 0
+#endif
+__host__ __device__ constexpr int stage_rows(int nch) {
+    return ROAR_STAGE_ROWS <= 0 ? 0
+           : nch <= 2          ? ROAR_STAGE_ROWS
+                               : (ROAR_STAGE_ROWS * 2 / nch > 0 ? ROAR_STAGE_ROWS * 2 / nch : 1);
+}
+__host__ __device__ inline size_t search_stage_bytes(int dtype, int d, int tw) {
+    if (dtype != 0 || tw != 1) return 0;
+    return (size_t)2 * stage_rows(search_nch(d)) * (size_t)(d >> 2) * 16;
+}
+
+// Per team: the above plus a 16-byte control block (claimed query, hop count,
+// pool size), then `stage` bytes of gather staging.
+__host__ __device__ inline size_t search_smem_per_team(int lcap, int hash_log2, size_t stage = 0) {
+    return search_smem_per_warp(lcap, hash_log2) + 16 + stage;
 }
 // Resident CTAs per SM for this configuration with teams of tw warps (0 if it
 // cannot launch), the teams per CTA, and the launch itself.

@@ -7,10 +7,7 @@ namespace roar {
 
 namespace {
 
-int nch_for(int d) {
-    const int need = ((d >> 2) + 31) / 32;
-    return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
-}
+int nch_for(int d) { return search_nch(d); }
 
 int threads_for(int tw) { return 32 * (tw > kWarpsPerBlock ? tw : kWarpsPerBlock); }
 
@@ -45,7 +42,7 @@ int hash_log2_for(int L) {
 int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, int tw) {
     const void *fn = search_kernel(dtype, d, rmax, tw);
     if (!fn) return 0;
-    const size_t smem = search_smem_per_team(lcap, hash_log2) * teams_per_block(tw);
+    const size_t smem = search_smem_per_team(lcap, hash_log2, search_stage_bytes(dtype, d, tw)) * teams_per_block(tw);
     if (smem > 227 * 1024) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
@@ -59,7 +56,8 @@ int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, in
 cudaError_t launch_search(const SearchArgs &a, int blocks, int tw, cudaStream_t s, bool configure) {
     const void *fn = search_kernel(a.dtype, a.d, a.rmax, tw);
     if (!fn || blocks <= 0) return cudaErrorInvalidValue;
-    const size_t smem = search_smem_per_team(a.lcap, a.hash_log2) * teams_per_block(tw);
+    const size_t smem =
+        search_smem_per_team(a.lcap, a.hash_log2, search_stage_bytes(a.dtype, a.d, tw)) * teams_per_block(tw);
     cudaError_t e = cudaSuccess;
     if (configure) {  // already done by search_blocks_per_sm when planning
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -35,6 +35,17 @@ __device__ __forceinline__ bool less_entry(float da, uint32_t ia, float db, uint
     return da < db || (da == db && ia < ib);
 }
 
+// 16 bytes global -> shared, asynchronous, cached in L2 only.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ float4 ld_stream_f4(const float4 *p) {
     float4 v;
     asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
@@ -192,6 +203,73 @@ __device__ __forceinline__ void score_rows(const void *base, const float *scales
     __syncwarp();
 }
 
+// FP32 distances for rows ids_s[0..cnt) through shared memory (one warp):
+// each lane copies its own 16-byte chunks (chunk c on lane c % 32, as in
+// score_rows) of S rows at a time into one of two buffers with cp.async, so
+// the next S rows are in flight while these are scored, and reads back only
+// those chunks: no lane waits for another before scoring. The arithmetic and
+// its order are score_rows' exactly.
+template <int NCH, int S>
+__device__ __forceinline__ void score_rows_staged(const float *base, int d, int d4, const float4 (&qr)[NCH],
+                                                  const uint32_t *ids_s, int cnt, float *out_s, int lane,
+                                                  float4 *stg) {
+    const int nb = (cnt + S - 1) / S;
+    auto issue = [&](int bi) {
+        float4 *buf = stg + (size_t)(bi & 1) * S * d4;
+        const int j0 = bi * S;
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            if (j0 + r < cnt) {
+                const float4 *row = reinterpret_cast<const float4 *>(base + (size_t)(ids_s[j0 + r] & kIdMask) * d);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const int ch = lane + 32 * c;
+                    if (ch < d4) cp_async16(buf + r * d4 + ch, row + ch);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    if (nb > 0) issue(0);
+    for (int bi = 0; bi < nb; ++bi) {
+        if (bi + 1 < nb) {
+            issue(bi + 1);   // into the buffer scored two batches ago (its reads are done)
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const float4 *buf = stg + (size_t)(bi & 1) * S * d4;
+        const int j0 = bi * S;
+        float sc[S];
+#pragma unroll
+        for (int r = 0; r < S; ++r) {
+            sc[r] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int ch = lane + 32 * c;
+                if (ch < d4) {
+                    const float4 x = buf[r * d4 + ch];
+                    sc[r] = fmaf(qr[c].x, x.x, sc[r]);
+                    sc[r] = fmaf(qr[c].y, x.y, sc[r]);
+                    sc[r] = fmaf(qr[c].z, x.z, sc[r]);
+                    sc[r] = fmaf(qr[c].w, x.w, sc[r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+            for (int r = 0; r < S; ++r) sc[r] = sc[r] + __shfl_xor_sync(kFull, sc[r], o);
+        }
+        float mine = sc[0];
+#pragma unroll
+        for (int r = 1; r < S; ++r)
+            if (lane == r) mine = sc[r];
+        if (lane < S && j0 + lane < cnt) out_s[j0 + lane] = -mine;
+    }
+    __syncwarp();
+}
+
 __device__ __forceinline__ uint32_t hash_slot(uint32_t u, int log2) {
     return (u * 2654435761u) >> (32 - log2);
 }
@@ -318,7 +396,10 @@ beam_search_kernel(const SearchArgs a) {
     const int lcap = a.lcap;
     const int hlog2 = a.hash_log2;           // 0: no shared table
     const int H = hlog2 ? (1 << hlog2) : 0;
-    unsigned char *tbase = smem_raw + (size_t)team * search_smem_per_team(lcap, hlog2);
+    constexpr int S = (DT == 0 && TW == 1) ? stage_rows(NCH) : 0;  // staged FP32 gather rows
+    const size_t stage = S ? (size_t)2 * S * (a.d >> 2) * 16 : 0;
+    unsigned char *tbase = smem_raw + (size_t)team * search_smem_per_team(lcap, hlog2, stage);
+    float4 *stg = reinterpret_cast<float4 *>(tbase + search_smem_per_team(lcap, hlog2, 0));
     float *pd = reinterpret_cast<float *>(tbase);
     uint32_t *pi = reinterpret_cast<uint32_t *>(pd + lcap);
     float *cd = reinterpret_cast<float *>(pi + lcap);
@@ -507,7 +588,11 @@ beam_search_kernel(const SearchArgs a) {
             if (cnt == 0) continue;
 
             // Gather + score: warp wt takes row groups wt, wt + TW, ...
-            score_rows<DT, NCH, B>(a.trav, a.scales, d, d4, qr, ci, cnt, cd, lane, wt * B, TW * B);
+            if constexpr (S > 0) {
+                score_rows_staged<NCH, S>(static_cast<const float *>(a.trav), d, d4, qr, ci, cnt, cd, lane, stg);
+            } else {
+                score_rows<DT, NCH, B>(a.trav, a.scales, d, d4, qr, ci, cnt, cd, lane, wt * B, TW * B);
+            }
             tsync();
             if (!leader) continue;
 
