@@ -89,19 +89,28 @@ __host__ __device__ inline int search_nch(int d) {
     return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
 }
 
-// The FP32 one-warp kernel stages its row gathers in shared memory: two
-// buffers of stage_rows(NCH) rows per warp (ROAR_STAGE_ROWS rows for d <= 256,
-// proportionally fewer for wider rows; 0 turns staging off).
+// For short searches the FP32 one-warp kernel stages its row gathers in
+// shared memory: two buffers of stage_rows(NCH) rows per warp (ROAR_STAGE_ROWS
+// rows for d <= 256, proportionally fewer for wider rows). Measured on GB300
+// (1M x 200): 4 rows are 3-8 % faster at L = 50-150 and equal at L = 300; for
+// longer pools the extra shared memory costs more occupancy than it gains, so
+// the staged variant runs only while lcap <= ROAR_STAGE_MAX_LCAP.
 #ifndef ROAR_STAGE_ROWS
-#define ROAR_STAGE_ROWS 0
+#define ROAR_STAGE_ROWS 4
+#endif
+#ifndef ROAR_STAGE_MAX_LCAP
+#define ROAR_STAGE_MAX_LCAP 320
 #endif
 __host__ __device__ constexpr int stage_rows(int nch) {
     return ROAR_STAGE_ROWS <= 0 ? 0
            : nch <= 2          ? ROAR_STAGE_ROWS
                                : (ROAR_STAGE_ROWS * 2 / nch > 0 ? ROAR_STAGE_ROWS * 2 / nch : 1);
 }
-__host__ __device__ inline size_t search_stage_bytes(int dtype, int d, int tw) {
-    if (dtype != 0 || tw != 1) return 0;
+__host__ __device__ inline bool search_staged(int dtype, int tw, int lcap) {
+    return dtype == 0 && tw == 1 && lcap <= ROAR_STAGE_MAX_LCAP && ROAR_STAGE_ROWS > 0;
+}
+__host__ __device__ inline size_t search_stage_bytes(int dtype, int d, int tw, int lcap) {
+    if (!search_staged(dtype, tw, lcap)) return 0;
     return (size_t)2 * stage_rows(search_nch(d)) * (size_t)(d >> 2) * 16;
 }
 
@@ -116,7 +125,7 @@ int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, in
 int teams_per_block(int tw);
 cudaError_t launch_search(const SearchArgs &a, int blocks, int tw, cudaStream_t s, bool configure = true);
 template <int DT>
-const void *kernel_table(int nch, int rpl, int tw);
+const void *kernel_table(int nch, int rpl, int tw, bool staged);
 
 int hash_log2_for(int L);
 

@@ -2,5 +2,5 @@
 #include "roar_search_kernel.cuh"
 
 namespace roar {
-template const void *kernel_table<2>(int nch, int rpl, int tw);
+template const void *kernel_table<2>(int nch, int rpl, int tw, bool staged);
 }  // namespace roar

@@ -379,7 +379,9 @@ struct TeamShape {
 // products, so every distance is computed exactly as with one warp.
 // RPL = adjacency ids per lane (rmax <= 32 * RPL), which also bounds the new
 // candidates of one hop.
-template <int DT, int NCH, int RPL, int TW>
+// STG > 0 (FP32, one warp per query): the hop's rows are gathered through
+// shared memory, STG rows per buffer (score_rows_staged).
+template <int DT, int NCH, int RPL, int TW, int STG>
 __global__ void __launch_bounds__(TeamShape<DT, TW>::kThreads, TeamShape<DT, TW>::kMinBlocks)
 beam_search_kernel(const SearchArgs a) {
     constexpr int kMaxRowPerLane = RPL;
@@ -396,7 +398,8 @@ beam_search_kernel(const SearchArgs a) {
     const int lcap = a.lcap;
     const int hlog2 = a.hash_log2;           // 0: no shared table
     const int H = hlog2 ? (1 << hlog2) : 0;
-    constexpr int S = (DT == 0 && TW == 1) ? stage_rows(NCH) : 0;  // staged FP32 gather rows
+    static_assert(STG == 0 || (DT == 0 && TW == 1), "staging is for the FP32 one-warp kernel");
+    constexpr int S = STG;  // staged FP32 gather rows per buffer (0: registers)
     const size_t stage = S ? (size_t)2 * S * (a.d >> 2) * 16 : 0;
     unsigned char *tbase = smem_raw + (size_t)team * search_smem_per_team(lcap, hlog2, stage);
     float4 *stg = reinterpret_cast<float4 *>(tbase + search_smem_per_team(lcap, hlog2, 0));
@@ -750,16 +753,22 @@ beam_search_kernel(const SearchArgs a) {
 
 }  // namespace
 
-// Kernel for (row chunks per lane, adjacency ids per lane, warps per team).
+// Kernel for (row chunks per lane, adjacency ids per lane, warps per team,
+// staged gather: FP32 one-warp kernels only).
 template <int DT>
-const void *kernel_table(int nch, int rpl, int tw) {
+const void *kernel_table(int nch, int rpl, int tw, bool staged) {
 #define ROAR_K(N, R, T) \
-    if (nch == N && rpl == R && tw == T) return (const void *)beam_search_kernel<DT, N, R, T>;
-#define ROAR_KT(N, R) ROAR_K(N, R, 1) ROAR_K(N, R, 2) ROAR_K(N, R, 4) ROAR_K(N, R, 8)
+    if (nch == N && rpl == R && tw == T && !staged) return (const void *)beam_search_kernel<DT, N, R, T, 0>;
+#define ROAR_KS(N, R)                                                                                     \
+    if constexpr (DT == 0) {                                                                              \
+        if (nch == N && rpl == R && tw == 1 && staged) return (const void *)beam_search_kernel<0, N, R, 1, stage_rows(N)>; \
+    }
+#define ROAR_KT(N, R) ROAR_K(N, R, 1) ROAR_K(N, R, 2) ROAR_K(N, R, 4) ROAR_K(N, R, 8) ROAR_KS(N, R)
 #define ROAR_KN(N) ROAR_KT(N, 2) ROAR_KT(N, 4)
     ROAR_KN(1) ROAR_KN(2) ROAR_KN(4) ROAR_KN(8)
 #undef ROAR_KN
 #undef ROAR_KT
+#undef ROAR_KS
 #undef ROAR_K
     return nullptr;
 }

@@ -31,6 +31,15 @@ def test_tiny_k_and_L_edges(tiny, tiny_idx, k, L):
     assert_same(run(tiny_idx, Q, k, L), ref, f"k={k} L={L}")
 
 
+@pytest.mark.parametrize("L", [320, 321])
+def test_staged_and_register_gather_edge(tiny, tiny_idx, L):
+    """Pools up to 320 entries gather rows through shared memory, longer ones
+    through registers; both give the oracle's trajectory."""
+    Q = tiny["Q"][:150]
+    ref = oracle.beam_search(tiny["X"], tiny["adj"], tiny["entry"], Q, 10, L, max_visits=MV)
+    assert_same(run(tiny_idx, Q, 10, L), ref, f"L={L}")
+
+
 @pytest.mark.parametrize("nq", [1, 2, 5, 129])
 def test_ragged_batches(tiny, tiny_idx, nq):
     Q = tiny["Q"][:nq]
