@@ -142,21 +142,27 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+// Issue a load of 32 consecutive FP32 columns of this thread's TMEM lane; the
+// registers are valid only after tc_wait_ld.
+__device__ __forceinline__ void tc_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+
+// Wait for this thread's TMEM loads. The registers of the loads pass through
+// the statement, so no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tc_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// Orders later uses of `r` after the preceding (volatile) wait.
+__device__ __forceinline__ void reg_after_wait(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
 }
 
 // Order-preserving map of a finite float to uint32 (larger float, larger key).
@@ -354,15 +360,42 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
             const int64_t n0 = t * kTN;
             const int lim = (int)((n - n0) < kTN ? (n - n0) : kTN);
 #pragma unroll 1
-            for (int cb = 0; cb < kTN; cb += 32) {
-                float v[32];
-                tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTN + cb), v);
+            for (int cb = 0; cb < kTN; cb += 64) {
+                uint32_t ra[32], rb[32];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTN + cb);
+                tc_ld32_issue(taddr, ra);
+                tc_ld32_issue(taddr + 32, rb);
+                tc_wait_ld(ra);
+                reg_after_wait(rb);
                 if (!row_ok) continue;
+                // Most 64-column groups hold nothing above the row's threshold
+                // once the first tiles have set it: test their maximum first.
+                float mp[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) mp[i] = fmaxf(__uint_as_float(ra[i]), __uint_as_float(rb[i]));
+#pragma unroll
+                for (int j = 8; j < 32; ++j) {
+                    mp[j & 7] = fmaxf(mp[j & 7], __uint_as_float(ra[j]));
+                    mp[j & 7] = fmaxf(mp[j & 7], __uint_as_float(rb[j]));
+                }
+                const float m = fmaxf(fmaxf(fmaxf(mp[0], mp[1]), fmaxf(mp[2], mp[3])),
+                                      fmaxf(fmaxf(mp[4], mp[5]), fmaxf(mp[6], mp[7])));
+                if (!(m > thr)) continue;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    if (v[j] > thr && cb + j < lim) {
-                        rs[cnt] = v[j];
+                    const float v = __uint_as_float(ra[j]);
+                    if (v > thr && cb + j < lim) {
+                        rs[cnt] = v;
                         ri[cnt] = (uint32_t)(n0 + cb + j);
+                        ++cnt;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float v = __uint_as_float(rb[j]);
+                    if (v > thr && cb + 32 + j < lim) {
+                        rs[cnt] = v;
+                        ri[cnt] = (uint32_t)(n0 + cb + 32 + j);
                         ++cnt;
                     }
                 }
