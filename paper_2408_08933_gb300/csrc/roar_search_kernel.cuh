@@ -365,11 +365,11 @@ __device__ __forceinline__ int lower_bound_entries(const float *dv, const uint32
 
 // Launch shape of a team of TW warps per query: CTAs of max(4, TW) warps,
 // with the register budget of min_blocks_per_sm<DT>() 4-warp CTAs per SM.
-template <int DT, int TW>
+template <int DT, int TW, int STG = 0>
 struct TeamShape {
     static constexpr int kThreads = 32 * (TW > kWarpsPerBlock ? TW : kWarpsPerBlock);
     static constexpr int kTeams = kThreads / (32 * TW);
-    static constexpr int kWarpBudget = min_blocks_per_sm<DT>() * kWarpsPerBlock;
+    static constexpr int kWarpBudget = (STG > 0 ? ROAR_MIN_BLOCKS_STAGED : min_blocks_per_sm<DT>()) * kWarpsPerBlock;
     static constexpr int kMinBlocks = (kWarpBudget * 32) / kThreads > 0 ? (kWarpBudget * 32) / kThreads : 1;
 };
 
@@ -382,7 +382,7 @@ struct TeamShape {
 // STG > 0 (FP32, one warp per query): the hop's rows are gathered through
 // shared memory, STG rows per buffer (score_rows_staged).
 template <int DT, int NCH, int RPL, int TW, int STG>
-__global__ void __launch_bounds__(TeamShape<DT, TW>::kThreads, TeamShape<DT, TW>::kMinBlocks)
+__global__ void __launch_bounds__(TeamShape<DT, TW, STG>::kThreads, TeamShape<DT, TW, STG>::kMinBlocks)
 beam_search_kernel(const SearchArgs a) {
     constexpr int kMaxRowPerLane = RPL;
     constexpr int kMaxCandPerLane = RPL;
