@@ -89,34 +89,48 @@ __host__ __device__ inline int search_nch(int d) {
     return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
 }
 
-// For short searches the FP32 one-warp kernel stages its row gathers in
-// shared memory: two buffers of stage_rows(NCH) rows per warp (ROAR_STAGE_ROWS
-// rows for d <= 256, proportionally fewer for wider rows). Measured on GB300
-// (1M x 200): 4 rows are 3-8 % faster at L = 50-150 and equal at L = 300; for
-// longer pools the extra shared memory costs more occupancy than it gains, so
-// the staged variant runs only while lcap <= ROAR_STAGE_MAX_LCAP.
+// For short searches the one-warp kernels stage their row gathers in shared
+// memory: two buffers of stage_rows(dtype, NCH) rows per warp (FP32:
+// ROAR_STAGE_ROWS rows for d <= 256, BF16 / FP8: ROAR_STAGE_ROWS_LOWP;
+// proportionally fewer for wider rows). Measured on GB300 (1M x 200), FP32
+// with 4 rows: 3-8 % faster at L = 50-150 and equal at L = 300; for longer
+// pools the extra shared memory costs more occupancy than it gains, so the
+// staged variants run only while lcap <= ROAR_STAGE_MAX_LCAP.
 #ifndef ROAR_STAGE_ROWS
 #define ROAR_STAGE_ROWS 4
+#endif
+#ifndef ROAR_STAGE_ROWS_LOWP
+#define ROAR_STAGE_ROWS_LOWP 8
 #endif
 #ifndef ROAR_STAGE_MAX_LCAP
 #define ROAR_STAGE_MAX_LCAP 320
 #endif
-// Register budget of the staged kernel, in 4-warp CTAs per SM: 5 (96
+// Register budget of the staged FP32 kernel, in 4-warp CTAs per SM: 5 (96
 // registers, no spills) measured 3.5 % faster at L = 90 than 4, 6 and 8.
 #ifndef ROAR_MIN_BLOCKS_STAGED
 #define ROAR_MIN_BLOCKS_STAGED 5
 #endif
-__host__ __device__ constexpr int stage_rows(int nch) {
-    return ROAR_STAGE_ROWS <= 0 ? 0
-           : nch <= 2          ? ROAR_STAGE_ROWS
-                               : (ROAR_STAGE_ROWS * 2 / nch > 0 ? ROAR_STAGE_ROWS * 2 / nch : 1);
+// Bytes of one 4-element row chunk: FP32 16, BF16 8, FP8 4.
+__host__ __device__ constexpr int chunk_bytes(int dtype) { return 16 >> dtype; }
+__host__ __device__ constexpr int stage_rows(int dtype, int nch) {
+    return (dtype == 0 ? ROAR_STAGE_ROWS : ROAR_STAGE_ROWS_LOWP) <= 0 ? 0
+           : nch <= 2 ? (dtype == 0 ? ROAR_STAGE_ROWS : ROAR_STAGE_ROWS_LOWP)
+           : ((dtype == 0 ? ROAR_STAGE_ROWS : ROAR_STAGE_ROWS_LOWP) * 2 / nch > 0
+                  ? (dtype == 0 ? ROAR_STAGE_ROWS : ROAR_STAGE_ROWS_LOWP) * 2 / nch
+                  : 1);
+}
+// Staging bytes per warp for S rows per buffer: two buffers of S rows of d4
+// chunks, then (FP8) two buffers of S row scales; a multiple of 16.
+__host__ __device__ inline size_t stage_bytes(int dtype, int S, int d4) {
+    const size_t b = (size_t)2 * S * d4 * chunk_bytes(dtype) + (dtype == 2 ? (size_t)2 * S * 4 : 0);
+    return (b + 15) / 16 * 16;
 }
 __host__ __device__ inline bool search_staged(int dtype, int tw, int lcap) {
-    return dtype == 0 && tw == 1 && lcap <= ROAR_STAGE_MAX_LCAP && ROAR_STAGE_ROWS > 0;
+    return tw == 1 && lcap <= ROAR_STAGE_MAX_LCAP && stage_rows(dtype, 1) > 0;
 }
 __host__ __device__ inline size_t search_stage_bytes(int dtype, int d, int tw, int lcap) {
     if (!search_staged(dtype, tw, lcap)) return 0;
-    return (size_t)2 * stage_rows(search_nch(d)) * (size_t)(d >> 2) * 16;
+    return stage_bytes(dtype, stage_rows(dtype, search_nch(d)), d >> 2);
 }
 
 // Per team: the above plus a 16-byte control block (claimed query, hop count,

@@ -20,8 +20,8 @@ const void *search_kernel(int dtype, int d, int rmax, int tw, int lcap) {
     const bool staged = search_staged(dtype, tw, lcap);
     switch (dtype) {
         case 0: return kernel_table<0>(nch, rpl, tw, staged);
-        case 1: return kernel_table<1>(nch, rpl, tw, false);
-        case 2: return kernel_table<2>(nch, rpl, tw, false);
+        case 1: return kernel_table<1>(nch, rpl, tw, staged);
+        case 2: return kernel_table<2>(nch, rpl, tw, staged);
         default: return nullptr;
     }
 }

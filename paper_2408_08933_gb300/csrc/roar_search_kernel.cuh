@@ -40,6 +40,13 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
 }
+// 4 or 8 bytes global -> shared, asynchronous (cached in L1 and L2).
+template <int N>
+__device__ __forceinline__ void cp_async_small(void *smem_dst, const void *gsrc) {
+    static_assert(N == 4 || N == 8, "cp.async.ca sizes");
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gsrc), "n"(N) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -203,28 +210,41 @@ __device__ __forceinline__ void score_rows(const void *base, const float *scales
     __syncwarp();
 }
 
-// FP32 distances for rows ids_s[0..cnt) through shared memory (one warp):
-// each lane copies its own 16-byte chunks (chunk c on lane c % 32, as in
-// score_rows) of S rows at a time into one of two buffers with cp.async, so
-// the next S rows are in flight while these are scored, and reads back only
-// those chunks: no lane waits for another before scoring. The arithmetic and
-// its order are score_rows' exactly.
-template <int NCH, int S>
-__device__ __forceinline__ void score_rows_staged(const float *base, int d, int d4, const float4 (&qr)[NCH],
-                                                  const uint32_t *ids_s, int cnt, float *out_s, int lane,
-                                                  float4 *stg) {
+// Distances for rows ids_s[0..cnt) through shared memory (one warp): each
+// lane copies its own row chunks (chunk c on lane c % 32, as in score_rows),
+// and for FP8 lane r the scale of row r, for S rows at a time into one of two
+// buffers with cp.async, so the next S rows are in flight while these are
+// scored, and reads back only what it copied: no lane waits for another. The
+// decode, the arithmetic and its order are score_rows' exactly.
+template <int DT, int NCH, int S>
+__device__ __forceinline__ void score_rows_staged(const void *base, const float *scales, int d4,
+                                                  const float4 (&qr)[NCH], const uint32_t *ids_s, int cnt,
+                                                  float *out_s, int lane, unsigned char *stg) {
+    using Chunk = decltype(RawChunk<DT>::v);
+    constexpr int CB = (int)sizeof(Chunk);
+    static_assert(CB == chunk_bytes(DT), "chunk size");
+    Chunk *cbuf = reinterpret_cast<Chunk *>(stg);
+    float *sbuf = reinterpret_cast<float *>(stg + (size_t)2 * S * d4 * CB);   // FP8 row scales
+    const Chunk *rows = static_cast<const Chunk *>(base);
     const int nb = (cnt + S - 1) / S;
     auto issue = [&](int bi) {
-        float4 *buf = stg + (size_t)(bi & 1) * S * d4;
+        Chunk *buf = cbuf + (size_t)(bi & 1) * S * d4;
         const int j0 = bi * S;
 #pragma unroll
         for (int r = 0; r < S; ++r) {
             if (j0 + r < cnt) {
-                const float4 *row = reinterpret_cast<const float4 *>(base + (size_t)(ids_s[j0 + r] & kIdMask) * d);
+                const uint32_t u = ids_s[j0 + r] & kIdMask;
+                const Chunk *row = rows + (size_t)u * d4;
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
                     const int ch = lane + 32 * c;
-                    if (ch < d4) cp_async16(buf + r * d4 + ch, row + ch);
+                    if (ch < d4) {
+                        if constexpr (CB == 16) cp_async16(buf + r * d4 + ch, row + ch);
+                        else cp_async_small<CB>(buf + r * d4 + ch, row + ch);
+                    }
+                }
+                if constexpr (DT == 2) {
+                    if (lane == r && scales) cp_async_small<4>(sbuf + (bi & 1) * S + r, scales + u);
                 }
             }
         }
@@ -238,7 +258,7 @@ __device__ __forceinline__ void score_rows_staged(const float *base, int d, int 
         } else {
             cp_async_wait<0>();
         }
-        const float4 *buf = stg + (size_t)(bi & 1) * S * d4;
+        const Chunk *buf = cbuf + (size_t)(bi & 1) * S * d4;
         const int j0 = bi * S;
         float sc[S];
 #pragma unroll
@@ -248,7 +268,9 @@ __device__ __forceinline__ void score_rows_staged(const float *base, int d, int 
             for (int c = 0; c < NCH; ++c) {
                 const int ch = lane + 32 * c;
                 if (ch < d4) {
-                    const float4 x = buf[r * d4 + ch];
+                    RawChunk<DT> raw;
+                    raw.v = buf[r * d4 + ch];
+                    const float4 x = to_f4<DT>(raw);
                     sc[r] = fmaf(qr[c].x, x.x, sc[r]);
                     sc[r] = fmaf(qr[c].y, x.y, sc[r]);
                     sc[r] = fmaf(qr[c].z, x.z, sc[r]);
@@ -265,7 +287,14 @@ __device__ __forceinline__ void score_rows_staged(const float *base, int d, int 
 #pragma unroll
         for (int r = 1; r < S; ++r)
             if (lane == r) mine = sc[r];
-        if (lane < S && j0 + lane < cnt) out_s[j0 + lane] = -mine;
+        if (lane < S && j0 + lane < cnt) {
+            if constexpr (DT == 2) {
+                const float s8 = scales ? sbuf[(bi & 1) * S + lane] : 1.0f;
+                out_s[j0 + lane] = -(s8 * mine);
+            } else {
+                out_s[j0 + lane] = -mine;
+            }
+        }
     }
     __syncwarp();
 }
@@ -369,7 +398,8 @@ template <int DT, int TW, int STG = 0>
 struct TeamShape {
     static constexpr int kThreads = 32 * (TW > kWarpsPerBlock ? TW : kWarpsPerBlock);
     static constexpr int kTeams = kThreads / (32 * TW);
-    static constexpr int kWarpBudget = (STG > 0 ? ROAR_MIN_BLOCKS_STAGED : min_blocks_per_sm<DT>()) * kWarpsPerBlock;
+    static constexpr int kWarpBudget =
+        (STG > 0 && DT == 0 ? ROAR_MIN_BLOCKS_STAGED : min_blocks_per_sm<DT>()) * kWarpsPerBlock;
     static constexpr int kMinBlocks = (kWarpBudget * 32) / kThreads > 0 ? (kWarpBudget * 32) / kThreads : 1;
 };
 
@@ -379,8 +409,8 @@ struct TeamShape {
 // products, so every distance is computed exactly as with one warp.
 // RPL = adjacency ids per lane (rmax <= 32 * RPL), which also bounds the new
 // candidates of one hop.
-// STG > 0 (FP32, one warp per query): the hop's rows are gathered through
-// shared memory, STG rows per buffer (score_rows_staged).
+// STG > 0 (one warp per query): the hop's rows are gathered through shared
+// memory, STG rows per buffer (score_rows_staged).
 template <int DT, int NCH, int RPL, int TW, int STG>
 __global__ void __launch_bounds__(TeamShape<DT, TW, STG>::kThreads, TeamShape<DT, TW, STG>::kMinBlocks)
 beam_search_kernel(const SearchArgs a) {
@@ -398,11 +428,11 @@ beam_search_kernel(const SearchArgs a) {
     const int lcap = a.lcap;
     const int hlog2 = a.hash_log2;           // 0: no shared table
     const int H = hlog2 ? (1 << hlog2) : 0;
-    static_assert(STG == 0 || (DT == 0 && TW == 1), "staging is for the FP32 one-warp kernel");
-    constexpr int S = STG;  // staged FP32 gather rows per buffer (0: registers)
-    const size_t stage = S ? (size_t)2 * S * (a.d >> 2) * 16 : 0;
+    static_assert(STG == 0 || TW == 1, "staging is for one-warp kernels");
+    constexpr int S = STG;  // staged gather rows per buffer (0: registers)
+    const size_t stage = S ? stage_bytes(DT, S, a.d >> 2) : 0;
     unsigned char *tbase = smem_raw + (size_t)team * search_smem_per_team(lcap, hlog2, stage);
-    float4 *stg = reinterpret_cast<float4 *>(tbase + search_smem_per_team(lcap, hlog2, 0));
+    unsigned char *stg = tbase + search_smem_per_team(lcap, hlog2, 0);
     float *pd = reinterpret_cast<float *>(tbase);
     uint32_t *pi = reinterpret_cast<uint32_t *>(pd + lcap);
     float *cd = reinterpret_cast<float *>(pi + lcap);
@@ -592,7 +622,7 @@ beam_search_kernel(const SearchArgs a) {
 
             // Gather + score: warp wt takes row groups wt, wt + TW, ...
             if constexpr (S > 0) {
-                score_rows_staged<NCH, S>(static_cast<const float *>(a.trav), d, d4, qr, ci, cnt, cd, lane, stg);
+                score_rows_staged<DT, NCH, S>(a.trav, a.scales, d4, qr, ci, cnt, cd, lane, stg);
             } else {
                 score_rows<DT, NCH, B>(a.trav, a.scales, d, d4, qr, ci, cnt, cd, lane, wt * B, TW * B);
             }
@@ -754,14 +784,15 @@ beam_search_kernel(const SearchArgs a) {
 }  // namespace
 
 // Kernel for (row chunks per lane, adjacency ids per lane, warps per team,
-// staged gather: FP32 one-warp kernels only).
+// staged gather: one-warp kernels only).
 template <int DT>
 const void *kernel_table(int nch, int rpl, int tw, bool staged) {
 #define ROAR_K(N, R, T) \
     if (nch == N && rpl == R && tw == T && !staged) return (const void *)beam_search_kernel<DT, N, R, T, 0>;
-#define ROAR_KS(N, R)                                                                                     \
-    if constexpr (DT == 0) {                                                                              \
-        if (nch == N && rpl == R && tw == 1 && staged) return (const void *)beam_search_kernel<0, N, R, 1, stage_rows(N)>; \
+#define ROAR_KS(N, R)                                                                              \
+    if constexpr (stage_rows(DT, N) > 0) {                                                         \
+        if (nch == N && rpl == R && tw == 1 && staged)                                             \
+            return (const void *)beam_search_kernel<DT, N, R, 1, stage_rows(DT, N)>;               \
     }
 #define ROAR_KT(N, R) ROAR_K(N, R, 1) ROAR_K(N, R, 2) ROAR_K(N, R, 4) ROAR_K(N, R, 8) ROAR_KS(N, R)
 #define ROAR_KN(N) ROAR_KT(N, 2) ROAR_KT(N, 4)

@@ -45,7 +45,7 @@ def test_quantizers_bit_exact(tiny, d):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
-@pytest.mark.parametrize("L", [10, 50, 100])
+@pytest.mark.parametrize("L", [10, 50, 100, 400])
 def test_quantized_search_bit_exact(tiny, dtype, L):
     X = tiny["X"]
     if dtype == "bf16":
