@@ -125,11 +125,14 @@ __host__ __device__ inline size_t stage_bytes(int dtype, int S, int d4) {
     const size_t b = (size_t)2 * S * d4 * chunk_bytes(dtype) + (dtype == 2 ? (size_t)2 * S * 4 : 0);
     return (b + 15) / 16 * 16;
 }
-__host__ __device__ inline bool search_staged(int dtype, int tw, int lcap) {
-    return tw == 1 && lcap <= ROAR_STAGE_MAX_LCAP && stage_rows(dtype, 1) > 0;
+// Rows are copied in 16-byte pieces, so a row's bytes must be a multiple of 16
+// (FP32: any d % 4 == 0; BF16: d % 8 == 0; FP8: d % 16 == 0).
+__host__ __device__ inline bool search_staged(int dtype, int d, int tw, int lcap) {
+    return tw == 1 && lcap <= ROAR_STAGE_MAX_LCAP && stage_rows(dtype, 1) > 0 &&
+           ((size_t)d * (4 >> dtype)) % 16 == 0;
 }
 __host__ __device__ inline size_t search_stage_bytes(int dtype, int d, int tw, int lcap) {
-    if (!search_staged(dtype, tw, lcap)) return 0;
+    if (!search_staged(dtype, d, tw, lcap)) return 0;
     return stage_bytes(dtype, stage_rows(dtype, search_nch(d)), d >> 2);
 }
 

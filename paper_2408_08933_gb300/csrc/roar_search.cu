@@ -17,7 +17,7 @@ int teams_per_block(int tw) { return threads_for(tw) / (32 * tw); }
 
 const void *search_kernel(int dtype, int d, int rmax, int tw, int lcap) {
     const int nch = nch_for(d), rpl = rmax <= 64 ? 2 : 4;
-    const bool staged = search_staged(dtype, tw, lcap);
+    const bool staged = search_staged(dtype, d, tw, lcap);
     switch (dtype) {
         case 0: return kernel_table<0>(nch, rpl, tw, staged);
         case 1: return kernel_table<1>(nch, rpl, tw, staged);

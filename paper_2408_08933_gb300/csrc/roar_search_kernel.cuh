@@ -210,12 +210,14 @@ __device__ __forceinline__ void score_rows(const void *base, const float *scales
     __syncwarp();
 }
 
-// Distances for rows ids_s[0..cnt) through shared memory (one warp): each
-// lane copies its own row chunks (chunk c on lane c % 32, as in score_rows),
-// and for FP8 lane r the scale of row r, for S rows at a time into one of two
-// buffers with cp.async, so the next S rows are in flight while these are
-// scored, and reads back only what it copied: no lane waits for another. The
-// decode, the arithmetic and its order are score_rows' exactly.
+// Distances for rows ids_s[0..cnt) through shared memory (one warp). The
+// warp copies S rows at a time, in 16-byte pieces (piece p on lane p % 32;
+// for FP8 lane r also the scale of row r), into one of two buffers with
+// cp.async, so the next S rows are in flight while these are scored. After
+// the copies land (each lane waits for its own, then the warp synchronises)
+// every lane reads its chunks (chunk c on lane c % 32, as in score_rows): the
+// decode, the arithmetic and its order are score_rows' exactly. Needs
+// 16-byte-aligned rows (d * element bytes a multiple of 16).
 template <int DT, int NCH, int S>
 __device__ __forceinline__ void score_rows_staged(const void *base, const float *scales, int d4,
                                                   const float4 (&qr)[NCH], const uint32_t *ids_s, int cnt,
@@ -223,25 +225,24 @@ __device__ __forceinline__ void score_rows_staged(const void *base, const float 
     using Chunk = decltype(RawChunk<DT>::v);
     constexpr int CB = (int)sizeof(Chunk);
     static_assert(CB == chunk_bytes(DT), "chunk size");
-    Chunk *cbuf = reinterpret_cast<Chunk *>(stg);
-    float *sbuf = reinterpret_cast<float *>(stg + (size_t)2 * S * d4 * CB);   // FP8 row scales
-    const Chunk *rows = static_cast<const Chunk *>(base);
+    const int rowbytes = d4 * CB;
+    const int pieces = rowbytes >> 4;                 // <= d4 <= 32 * NCH
+    unsigned char *cbuf = stg;
+    float *sbuf = reinterpret_cast<float *>(stg + (size_t)2 * S * rowbytes);   // FP8 row scales
+    const unsigned char *rows = static_cast<const unsigned char *>(base);
     const int nb = (cnt + S - 1) / S;
     auto issue = [&](int bi) {
-        Chunk *buf = cbuf + (size_t)(bi & 1) * S * d4;
+        unsigned char *buf = cbuf + (size_t)(bi & 1) * S * rowbytes;
         const int j0 = bi * S;
 #pragma unroll
         for (int r = 0; r < S; ++r) {
             if (j0 + r < cnt) {
                 const uint32_t u = ids_s[j0 + r] & kIdMask;
-                const Chunk *row = rows + (size_t)u * d4;
+                const unsigned char *row = rows + (size_t)u * rowbytes;
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
-                    const int ch = lane + 32 * c;
-                    if (ch < d4) {
-                        if constexpr (CB == 16) cp_async16(buf + r * d4 + ch, row + ch);
-                        else cp_async_small<CB>(buf + r * d4 + ch, row + ch);
-                    }
+                    const int p = lane + 32 * c;
+                    if (p < pieces) cp_async16(buf + r * rowbytes + p * 16, row + p * 16);
                 }
                 if constexpr (DT == 2) {
                     if (lane == r && scales) cp_async_small<4>(sbuf + (bi & 1) * S + r, scales + u);
@@ -253,23 +254,26 @@ __device__ __forceinline__ void score_rows_staged(const void *base, const float 
     if (nb > 0) issue(0);
     for (int bi = 0; bi < nb; ++bi) {
         if (bi + 1 < nb) {
-            issue(bi + 1);   // into the buffer scored two batches ago (its reads are done)
+            __syncwarp();    // every lane has read the buffer scored two batches ago
+            issue(bi + 1);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
-        const Chunk *buf = cbuf + (size_t)(bi & 1) * S * d4;
+        __syncwarp();        // the other lanes' pieces of this batch have landed too
+        const unsigned char *buf = cbuf + (size_t)(bi & 1) * S * rowbytes;
         const int j0 = bi * S;
         float sc[S];
 #pragma unroll
         for (int r = 0; r < S; ++r) {
             sc[r] = 0.0f;
+            const Chunk *rc = reinterpret_cast<const Chunk *>(buf + r * rowbytes);
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
                 const int ch = lane + 32 * c;
                 if (ch < d4) {
                     RawChunk<DT> raw;
-                    raw.v = buf[r * d4 + ch];
+                    raw.v = rc[ch];
                     const float4 x = to_f4<DT>(raw);
                     sc[r] = fmaf(qr[c].x, x.x, sc[r]);
                     sc[r] = fmaf(qr[c].y, x.y, sc[r]);
