@@ -89,8 +89,8 @@ __host__ __device__ inline int search_nch(int d) {
     return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
 }
 
-// For short searches the one-warp kernels stage their row gathers in shared
-// memory: two buffers of stage_rows(dtype, NCH) rows per warp (FP32:
+// For short searches the one-warp kernels can stage their row gathers in
+// shared memory: two buffers of stage_rows(dtype, NCH) rows per warp (FP32:
 // ROAR_STAGE_ROWS rows for d <= 256, BF16 / FP8: ROAR_STAGE_ROWS_LOWP;
 // proportionally fewer for wider rows). Measured on GB300 (1M x 200), FP32
 // with 4 rows: 3-8 % faster at L = 50-150 and equal at L = 300; for longer
@@ -99,8 +99,10 @@ __host__ __device__ inline int search_nch(int d) {
 #ifndef ROAR_STAGE_ROWS
 #define ROAR_STAGE_ROWS 4
 #endif
+// BF16 / FP8 staging is off by default: on GB300 (1M x 200, L = 50-300) it was
+// 5-30 % slower than their register path, which already gathers 8 rows per batch.
 #ifndef ROAR_STAGE_ROWS_LOWP
-#define ROAR_STAGE_ROWS_LOWP 8
+#define ROAR_STAGE_ROWS_LOWP 0
 #endif
 #ifndef ROAR_STAGE_MAX_LCAP
 #define ROAR_STAGE_MAX_LCAP 320
