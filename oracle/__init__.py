@@ -83,6 +83,8 @@ def _load():
         lib.orc_medoid.restype = i64
         lib.orc_acquire_neighbors.argtypes = [P, i64, i32, u32, P, i32, i32, i32, P]
         lib.orc_acquire_neighbors.restype = i32
+        lib.orc_acquire_neighbors_f32.argtypes = [P, i64, i32, u32, P, i32, i32, i32, P]
+        lib.orc_acquire_neighbors_f32.restype = i32
         lib.orc_build.argtypes = [P, i64, i64, i32, P, i32, i32, i32, u32, P, P, P]
         lib.orc_build.restype = ctypes.c_int
         _lib = lib
@@ -172,6 +174,20 @@ def acquire_neighbors(X, x: int, cand, M: int, fill: bool):
                                       1 if fill else 0, _p(res))
     if r < 0:
         raise ValueError("orc_acquire_neighbors: bad arguments")
+    return res[:r].copy()
+
+
+def acquire_neighbors_f32(X, x: int, cand, M: int, fill: bool):
+    """Alg. 3 with FP32 fixed-order distances (delta = -dot_fixed), ``cand`` in
+    the caller's order. Same steps as acquire_neighbors; only the precision of
+    the keep / drop comparisons differs."""
+    X = _f32(X)
+    cand = np.ascontiguousarray(cand, dtype=np.uint32)
+    res = np.empty(max(M, 1), dtype=np.uint32)
+    r = _load().orc_acquire_neighbors_f32(_p(X), X.shape[0], X.shape[1], x, _p(cand), cand.size, M,
+                                          1 if fill else 0, _p(res))
+    if r < 0:
+        raise ValueError("orc_acquire_neighbors_f32: bad arguments")
     return res[:r].copy()
 
 

@@ -506,6 +506,46 @@ int32_t orc_acquire_neighbors(const float *X, int64_t n, int32_t d, uint32_t x, 
     return r;
 }
 
+/* Alg. 3 again, with every distance in FP32 by the search's fixed order:
+ * delta(a, b) = -orc_dot_fixed(a, b). The paper fixes no precision for the
+ * pruning test; this form takes each keep / drop decision in the precision a
+ * GPU implementation takes it in (FP32, fixed summation order), so the two
+ * can be compared id for id. C is given as ids in the caller's order. */
+int32_t orc_acquire_neighbors_f32(const float *X, int64_t n, int32_t d, uint32_t x, const uint32_t *cand,
+                                  int32_t nc, int32_t M, int32_t fill, uint32_t *res) {
+    if ((int64_t)x >= n || nc < 0 || M <= 0) return -1;
+    for (int32_t i = 0; i < nc; ++i)
+        if ((int64_t)cand[i] >= n) return -1;
+    const float *xv = X + (int64_t)x * d;
+    int32_t nr = 0;
+    for (int32_t i = 0; i < nc && nr < M; ++i) {
+        const uint32_t c = cand[i];
+        if (c == x) continue;
+        int dup = 0;
+        for (int32_t j = 0; j < nr; ++j)
+            if (res[j] == c) dup = 1;
+        if (dup) continue;
+        if (nr == 0) { res[nr++] = c; continue; }            /* the closest candidate */
+        const float *cv = X + (int64_t)c * d;
+        const float dxc = -orc_dot_fixed(xv, cv, d);
+        int keep = 1;
+        for (int32_t j = 0; j < nr && keep; ++j)
+            if (!(dxc < -orc_dot_fixed(cv, X + (int64_t)res[j] * d, d))) keep = 0;
+        if (keep) res[nr++] = c;
+    }
+    if (fill) {
+        for (int32_t i = 0; i < nc && nr < M; ++i) {
+            const uint32_t c = cand[i];
+            if (c == x) continue;
+            int dup = 0;
+            for (int32_t j = 0; j < nr; ++j)
+                if (res[j] == c) dup = 1;
+            if (!dup) res[nr++] = c;
+        }
+    }
+    return nr;
+}
+
 /* Reverse-edge update of Alg. 2 and of Alg. 1's enhancement loop: give p the edge
  * p -> x. Skip when present; append when there is room; otherwise re-prune
  * N(p) U {x} with Alg. 3. */
