@@ -325,6 +325,35 @@ roar_status roar_medoid(const float *X_host, int64_t n, int32_t d, int32_t threa
                         uint32_t *entry);
 
 /*
+ * AcquireNeighbors (Alg. 3, Sec. 4.2.3) for nx nodes at once, one warp each:
+ * the candidates of node xs[i] are sorted by (delta(x, c), id) with
+ * delta(x, c) = -dot(x, c) in the search's fixed FP32 summation order; the
+ * first is kept, and each later candidate c is kept if delta(x, c) <
+ * delta(c, r) for every kept r (same precision and order); at most M are kept,
+ * and with fill the remaining budget is topped up from the other candidates in
+ * sorted order. Candidates equal to x and ids already kept are skipped.
+ *   X           device [n][d] FP32 rows, 16-byte aligned, d % 4 == 0, d <= 1024.
+ *   xs          device [nx] uint32 node ids.
+ *   cand        device [nx][cand_stride] uint32 candidate ids in any order;
+ *               0xFFFFFFFF entries are padding; cand_stride <= 1024.
+ *   ncand       device [nx] int32: entries of row i to read (clamped to
+ *               [0, cand_stride]).
+ *   M, fill     kept-list bound (1..64) and the fill flag.
+ *   out         device [nx][M] uint32 out: the kept ids in order, padded with
+ *               0xFFFFFFFF.
+ *   out_cnt     device [nx] int32 out: ids kept, or -1 when xs[i] or one of
+ *               its candidates is >= n (that row's out is all padding).
+ *   sorted_out  device [nx][cand_stride] uint32 out or NULL: the valid
+ *               candidates in the sorted order, padded with 0xFFFFFFFF.
+ * Asynchronous on `stream`; the caller owns every buffer. Errors: ROAR_EINVAL
+ * (sizes, pointers; checked before any launch), ROAR_ECUDA.
+ */
+roar_status roar_acquire(const float *X, int64_t n, int32_t d, const uint32_t *xs, int64_t nx,
+                         const uint32_t *cand, int32_t cand_stride, const int32_t *ncand, int32_t M,
+                         int32_t fill, uint32_t *out, int32_t *out_cnt, uint32_t *sorted_out,
+                         void *stream);
+
+/*
  * Build a RoarGraph index (Alg. 1): training-query kNN on the GPU (roar_knn,
  * depth nq_depth = N_q), bipartite graph, neighbourhood-aware projection with
  * AcquireNeighbors (Alg. 2, Alg. 3) on host threads, connectivity

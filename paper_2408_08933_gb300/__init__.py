@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.roar_knn.restype = ctypes.c_int
     L.roar_medoid.argtypes = [P, i64, i32, i32, ctypes.POINTER(u32)]
     L.roar_medoid.restype = ctypes.c_int
+    L.roar_acquire.argtypes = [P, i64, i32, P, i64, P, i32, P, i32, i32, P, P, P, P]
+    L.roar_acquire.restype = ctypes.c_int
     L.roar_build_index.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P,
                                    ctypes.POINTER(u32), P, P]
     L.roar_build_index.restype = ctypes.c_int
@@ -219,6 +221,12 @@ def roar_quantize(X, n, d, dtype, out, scales, stream=None):
 
 def roar_knn(T, nt, X, n, d, kk, ids, dist, stream=None):
     _check(lib().roar_knn(T, nt, X, n, d, kk, ids, dist, stream), "roar_knn")
+
+
+def roar_acquire(X, n, d, xs, nx, cand, cand_stride, ncand, M, fill, out, out_cnt, sorted_out=None,
+                 stream=None):
+    _check(lib().roar_acquire(X, n, d, xs, nx, cand, cand_stride, ncand, M, 1 if fill else 0, out, out_cnt,
+                              sorted_out, stream), "roar_acquire")
 
 
 def roar_medoid(X_host, n, d, threads=0):
@@ -377,6 +385,22 @@ def build_index(X, T, nq_depth=100, M=32, L_build=500, threads=0, stream=None):
     entry = roar_build_index(_ptr(X), n, d, _ptr(T), T.shape[0], nq_depth, M, L_build, threads,
                              _ptr(adj), st.ctypes.data, _stream_ptr(stream))
     return adj, entry, dict(zip(STAT_KEYS, st.tolist()))
+
+
+def acquire(X, xs, cand, ncand, M, fill, sorted_out=False, stream=None):
+    """Alg. 3 on the GPU for nodes xs [nx] (CUDA int32) with candidate rows
+    cand [nx, C] (CUDA int32, -1 = padding) of which ncand [nx] are read.
+    Returns (kept [nx, M] int32, counts [nx] int32[, sorted [nx, C] int32])."""
+    import torch
+
+    n, d = X.shape
+    nx, C = cand.shape
+    out = torch.empty((nx, M), dtype=torch.int32, device=X.device)
+    cnt = torch.empty(nx, dtype=torch.int32, device=X.device)
+    srt = torch.empty((nx, C), dtype=torch.int32, device=X.device) if sorted_out else None
+    roar_acquire(_ptr(X), n, d, _ptr(xs), nx, _ptr(cand), C, _ptr(ncand), M, fill, _ptr(out), _ptr(cnt),
+                 _ptr(srt) if srt is not None else None, _stream_ptr(stream))
+    return (out, cnt, srt) if sorted_out else (out, cnt)
 
 
 def knn(T, X, kk, stream=None):
