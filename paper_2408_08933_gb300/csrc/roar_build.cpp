@@ -449,16 +449,30 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
     std::vector<unsigned char> dirty((size_t)n, 1);  // rows whose merged form is stale
     double t_merge = 0, t_search = 0, t_prune = 0, t_rev = 0;
     {
-        uint32_t *pid = nullptr;
+        // Per chunk: search results (L_build ids) and the reverse edges each row
+        // has received (M ids) form that row's candidates for roar_acquire.
+        const int CS = L_build + M;
+        uint32_t *pid = nullptr, *cand = nullptr, *kept = nullptr, *xs = nullptr;
+        int32_t *ncand = nullptr, *kcnt = nullptr;
         float *pdist = nullptr;
         const int64_t max_chunk = std::min<int64_t>(n, std::min<int64_t>(524288, std::max<int64_t>(131072, n / 32)));
         e = cudaMalloc(&pid, (size_t)max_chunk * L_build * 4);
         if (e == cudaSuccess) e = cudaMalloc(&pdist, (size_t)max_chunk * L_build * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&cand, (size_t)max_chunk * CS * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&kept, (size_t)max_chunk * M * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&xs, (size_t)max_chunk * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&ncand, (size_t)max_chunk * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&kcnt, (size_t)max_chunk * 4);
+        std::vector<uint32_t> hxs((size_t)max_chunk);
+        std::vector<int32_t> hk((size_t)max_chunk);
+        if (e == cudaSuccess) {
+            std::vector<int32_t> nc((size_t)max_chunk, CS);
+            e = cudaMemcpyAsync(ncand, nc.data(), nc.size() * 4, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
         roar_index *gi = nullptr;
         if (e == cudaSuccess)
             rc = roar_index_create(n, d, X_dev, ROAR_F32, nullptr, nullptr, adj_dev, R, entry, 32768, &gi);
-        std::vector<uint32_t> hid((size_t)max_chunk * L_build);
-        std::vector<float> hd((size_t)max_chunk * L_build);
         int64_t q0 = 0;
         while (e == cudaSuccess && rc == ROAR_OK && q0 < n) {
             const int64_t qn = std::min(n - q0, std::min(max_chunk, std::max<int64_t>(1024, q0)));
@@ -475,33 +489,41 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
             rc = roar_search(gi, X_dev + (size_t)q0 * d, qn, L_build, L_build, pid, pdist, nullptr,
                              nullptr, nullptr, stream);
             if (rc != ROAR_OK) break;
-            e = cudaMemcpyAsync(hid.data(), pid, (size_t)qn * L_build * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(hd.data(), pdist, (size_t)qn * L_build * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) break;
             t_search += seconds_since(tp);
             tp = std::chrono::steady_clock::now();
+            // Candidate rows: [search results | received reverse edges, padded].
             parallel_for(qn, threads, [&](int64_t i, int) {
                 const int64_t x = q0 + i;
-                std::vector<Cand> C;
-                C.reserve((size_t)L_build + M);
-                for (int j = 0; j < L_build; ++j) {
-                    const uint32_t u = hid[(size_t)i * L_build + j];
-                    if (u == kNone || u == (uint32_t)x) continue;
-                    C.emplace_back(hd[(size_t)i * L_build + j], u);
-                }
-                const float *xv = X.data() + (size_t)x * d;
-                for (int j = 0; j < ce.cnt[x]; ++j) {  // reverse edges received so far
-                    const uint32_t u = ce.row(x)[j];
-                    bool dup = false;
-                    for (const Cand &c : C) dup |= c.second == u;
-                    if (!dup) C.emplace_back(neg_dot(xv, X.data() + (size_t)u * d, d), u);
-                }
-                std::sort(C.begin(), C.end(), cand_less);
-                ce.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, false, ce.row(x));
-                dirty[x] = 1;
+                uint32_t *r = ce.row(x);
+                for (int j = ce.cnt[x]; j < M; ++j) r[j] = kNone;
+                hxs[i] = (uint32_t)x;
             });
+            e = cudaMemcpy2DAsync(cand, (size_t)CS * 4, pid, (size_t)L_build * 4, (size_t)L_build * 4, (size_t)qn,
+                                  cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(cand + L_build, (size_t)CS * 4, ce.row(q0), (size_t)M * 4, (size_t)M * 4,
+                                      (size_t)qn, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(xs, hxs.data(), (size_t)qn * 4, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) break;
+            rc = roar_acquire(X_dev, n, d, xs, qn, cand, CS, ncand, M, 0, kept, kcnt, nullptr, stream);
+            if (rc != ROAR_OK) break;
+            e = cudaMemcpyAsync(ce.row(q0), kept, (size_t)qn * M * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hk.data(), kcnt, (size_t)qn * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            bool bad = false;
+            for (int64_t i = 0; i < qn; ++i) {
+                bad |= hk[i] < 0;
+                ce.cnt[q0 + i] = hk[i] < 0 ? 0 : hk[i];
+                dirty[q0 + i] = 1;
+            }
+            if (bad) {
+                set_error("roar_build_index: a search returned an id outside the base set");
+                rc = ROAR_EINVAL;
+                break;
+            }
             t_prune += seconds_since(tp);
             tp = std::chrono::steady_clock::now();
             add_reverse_edges(X.data(), d, M, false, threads, ce, 4 * L_build, q0, q0 + qn, &dirty);
@@ -513,6 +535,11 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         roar_index_destroy(gi);
         cudaFree(pid);
         cudaFree(pdist);
+        cudaFree(cand);
+        cudaFree(kept);
+        cudaFree(xs);
+        cudaFree(ncand);
+        cudaFree(kcnt);
         if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: enhancement search");
         if (rc != ROAR_OK) return rc;
     }
