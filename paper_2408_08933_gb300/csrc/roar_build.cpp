@@ -126,6 +126,54 @@ struct Lists {
     const uint32_t *row(int64_t i) const { return v.data() + (size_t)i * cap; }
 };
 
+// GPU re-pruning for reverse-edge rounds without fill: a target whose list
+// must be re-pruned and that received at most kGpuInc new edges in the round
+// is batched through roar_acquire (FP32 fixed-order distances); busier
+// targets (hubs) stay on the host.
+constexpr int kGpuInc = 96;
+struct GpuPrune {
+    const float *X_dev = nullptr;
+    int64_t n = 0;
+    int d = 0, M = 0, CS = 0;
+    int64_t rows = 0;  // batch capacity
+    uint32_t *cand = nullptr, *out = nullptr, *srt = nullptr, *xs = nullptr;
+    int32_t *nc = nullptr, *cnt = nullptr;
+    std::vector<uint32_t> hcand, hout, hsrt, hxs;
+    std::vector<int32_t> hnc, hcnt;
+    void *stream = nullptr;
+    cudaError_t init(const float *X, int64_t n_, int d_, int M_, int64_t rows_, void *stream_) {
+        X_dev = X;
+        n = n_;
+        d = d_;
+        M = M_;
+        CS = M_ + kGpuInc;
+        rows = rows_;
+        stream = stream_;
+        cudaError_t e = cudaMalloc(&cand, (size_t)rows * CS * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&srt, (size_t)rows * CS * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)rows * M * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&xs, (size_t)rows * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&nc, (size_t)rows * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&cnt, (size_t)rows * 4);
+        if (e != cudaSuccess) return e;
+        hcand.resize((size_t)rows * CS);
+        hsrt.resize((size_t)rows * CS);
+        hout.resize((size_t)rows * M);
+        hxs.resize((size_t)rows);
+        hnc.resize((size_t)rows);
+        hcnt.resize((size_t)rows);
+        return cudaSuccess;
+    }
+    ~GpuPrune() {
+        cudaFree(cand);
+        cudaFree(srt);
+        cudaFree(out);
+        cudaFree(xs);
+        cudaFree(nc);
+        cudaFree(cnt);
+    }
+};
+
 // Batched reverse-edge round (Alg. 2 and Alg. 1's enhancement loop) for the
 // forward edges of the sources x in [s0, s1): every node p gets p -> x for all
 // such x with p in fwd(x); lists over M are re-pruned with Alg. 3. Without
@@ -136,9 +184,11 @@ struct Lists {
 // A node that many lists point to (a hub) keeps at most `max_in` of its
 // reverse-edge candidates, the nearest ones, before pruning. Lists are
 // updated in place; nodes without incoming edges keep theirs. Every changed
-// node is flagged in `dirty` when it is given.
-void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lists &fwd, int max_in,
-                       int64_t s0, int64_t s1, std::vector<unsigned char> *dirty = nullptr) {
+// node is flagged in `dirty` when it is given. With `gpu` (no fill only), the
+// re-pruning of targets with at most kGpuInc new edges runs on the GPU.
+roar_status add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lists &fwd, int max_in,
+                              int64_t s0, int64_t s1, std::vector<unsigned char> *dirty = nullptr,
+                              GpuPrune *gpu = nullptr) {
     const int64_t n = fwd.n;
     std::vector<int64_t> off((size_t)n + 1, 0);
     for (int64_t x = s0; x < s1; ++x)
@@ -150,23 +200,32 @@ void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lis
         for (int j = 0; j < fwd.cnt[x]; ++j) inc[fillpos[fwd.row(x)[j]]++] = (uint32_t)x;
     fillpos.clear();
     fillpos.shrink_to_fit();
+    std::vector<unsigned char> on_gpu(gpu && !fill ? (size_t)n : 0, 0);
+    // own list first, then the incoming ids not in it (distinct, ascending)
+    auto gather = [&](int64_t p, std::vector<uint32_t> &all) {
+        const int nf = fwd.cnt[p];
+        all.assign(fwd.row(p), fwd.row(p) + nf);
+        for (int64_t k = off[p]; k < off[p + 1]; ++k) {
+            const uint32_t x = inc[k];
+            if (x == (uint32_t)p) continue;
+            if (std::find(all.begin(), all.begin() + nf, x) == all.begin() + nf) all.push_back(x);
+        }
+    };
     parallel_for(n, threads, [&](int64_t p, int) {
         if (off[p] == off[p + 1]) return;
         if (dirty) (*dirty)[p] = 1;
         const int nf = fwd.cnt[p];
-        std::vector<uint32_t> all(fwd.row(p), fwd.row(p) + nf);  // own list first
+        std::vector<uint32_t> all;
+        gather(p, all);
         const uint32_t *f = all.data();
-        // Incoming ids are distinct and ascending; only the own list can repeat them.
-        for (int64_t k = off[p]; k < off[p + 1]; ++k) {
-            const uint32_t x = inc[k];
-            if (x == (uint32_t)p) continue;
-            if (std::find(f, f + nf, x) == f + nf) all.push_back(x);
-            f = all.data();
-        }
         uint32_t *o = fwd.row(p);
         if ((int)all.size() <= M) {
             std::copy(all.begin(), all.end(), o);
             fwd.cnt[p] = (int)all.size();
+            return;
+        }
+        if (!on_gpu.empty() && (int)all.size() - nf <= kGpuInc) {
+            on_gpu[p] = 1;
             return;
         }
         std::vector<Cand> C;
@@ -191,6 +250,65 @@ void add_reverse_edges(const float *X, int d, int M, bool fill, int threads, Lis
         }
         fwd.cnt[p] = r;
     });
+    if (on_gpu.empty()) return ROAR_OK;
+    std::vector<uint32_t> rows;
+    for (int64_t p = 0; p < n; ++p)
+        if (on_gpu[p]) rows.push_back((uint32_t)p);
+    GpuPrune &g = *gpu;
+    cudaStream_t s = (cudaStream_t)g.stream;
+    for (size_t b0 = 0; b0 < rows.size(); b0 += (size_t)g.rows) {
+        const int64_t nb = (int64_t)std::min(rows.size() - b0, (size_t)g.rows);
+        parallel_for(nb, threads, [&](int64_t i, int) {
+            const int64_t p = rows[b0 + i];
+            std::vector<uint32_t> all;
+            gather(p, all);
+            uint32_t *r = g.hcand.data() + (size_t)i * g.CS;
+            std::copy(all.begin(), all.end(), r);
+            std::fill(r + all.size(), r + g.CS, kNone);
+            g.hxs[i] = (uint32_t)p;
+            g.hnc[i] = (int32_t)all.size();
+        });
+        cudaError_t e = cudaMemcpyAsync(g.cand, g.hcand.data(), (size_t)nb * g.CS * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.xs, g.hxs.data(), (size_t)nb * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.nc, g.hnc.data(), (size_t)nb * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return roar::cuda_fail(e, "roar_build_index: reverse-edge upload");
+        roar_status rc = roar_acquire(g.X_dev, g.n, g.d, g.xs, nb, g.cand, g.CS, g.nc, M, 0, g.out, g.cnt, g.srt,
+                                      g.stream);
+        if (rc != ROAR_OK) return rc;
+        e = cudaMemcpyAsync(g.hout.data(), g.out, (size_t)nb * M * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.hsrt.data(), g.srt, (size_t)nb * g.CS * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.hcnt.data(), g.cnt, (size_t)nb * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return roar::cuda_fail(e, "roar_build_index: reverse-edge prune");
+        std::atomic<bool> bad{false};
+        parallel_for(nb, threads, [&](int64_t i, int) {
+            const int64_t p = rows[b0 + i];
+            const uint32_t *f = g.hcand.data() + (size_t)i * g.CS;   // own list: the first nf ids
+            const int nf = fwd.cnt[p];
+            const uint32_t *srt = g.hsrt.data() + (size_t)i * g.CS;
+            const int r0 = g.hcnt[i];
+            if (r0 < 0) {
+                bad = true;
+                return;
+            }
+            uint32_t *o = fwd.row(p);
+            std::copy(g.hout.data() + (size_t)i * M, g.hout.data() + (size_t)i * M + r0, o);
+            int r = r0;
+            for (int j = 0; j < g.CS && r < M && srt[j] != kNone; ++j) {   // top-up: reverse edges, nearest first
+                const uint32_t c = srt[j];
+                if (c == (uint32_t)p) continue;
+                if (std::find(f, f + nf, c) != f + nf) continue;
+                if (std::find(o, o + r, c) != o + r) continue;
+                o[r++] = c;
+            }
+            fwd.cnt[p] = r;
+        });
+        if (bad) {
+            roar::set_error("roar_build_index: an edge points outside the base set");
+            return ROAR_EINVAL;
+        }
+    }
+    return ROAR_OK;
 }
 
 // Row x of the searched / final graph: N_pj(x) followed by the supplementary
@@ -397,7 +515,7 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
         pj.cnt[x] = acquire(X.data(), d, (uint32_t)x, C, M, true, pj.row(x));
     });
     // Alg. 2, reverse-edge step, batched.
-    add_reverse_edges(X.data(), d, M, true, threads, pj, 4 * L_build, 0, n);
+    if ((rc = add_reverse_edges(X.data(), d, M, true, threads, pj, 4 * L_build, 0, n)) != ROAR_OK) return rc;
     // The enhancement searches start at the medoid and walk G_pj: a medoid
     // that no pivot selected has no edges there and every search would stop
     // at once. Such a medoid gets a list as a pivot would, from its own
@@ -470,6 +588,8 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
             e = cudaMemcpyAsync(ncand, nc.data(), nc.size() * 4, cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
+        GpuPrune gprune;
+        if (e == cudaSuccess) e = gprune.init(X_dev, n, d, M, std::min<int64_t>(n, 262144), stream);
         roar_index *gi = nullptr;
         if (e == cudaSuccess)
             rc = roar_index_create(n, d, X_dev, ROAR_F32, nullptr, nullptr, adj_dev, R, entry, 32768, &gi);
@@ -526,7 +646,8 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
             }
             t_prune += seconds_since(tp);
             tp = std::chrono::steady_clock::now();
-            add_reverse_edges(X.data(), d, M, false, threads, ce, 4 * L_build, q0, q0 + qn, &dirty);
+            rc = add_reverse_edges(X.data(), d, M, false, threads, ce, 4 * L_build, q0, q0 + qn, &dirty, &gprune);
+            if (rc != ROAR_OK) break;
             t_rev += seconds_since(tp);
             q0 += qn;
             build_log("enhancement: searched %.0f of %.0f rows (%.1f s)", (double)q0, (double)n,
