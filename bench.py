@@ -315,7 +315,7 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
     res = {"mode": args.mode, "workload": w.name, "n": w.n, "d": w.d, "build": bstats}
     forms = {}
     if args.mode == "precision":
-        sweepL = [50, 75, 100, 150, 200, 300, 500, 1024]
+        sweepL = [50, 75, 100, 150, 200, 300, 400, 500, 1024]
         sample = np.random.default_rng(1).choice(nq, 200, replace=False)
         for dtype in ("f32", "bf16", "fp8"):
             if dtype == "f32":
