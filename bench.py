@@ -125,7 +125,7 @@ def _setup(w, torch, pkg, rs, log):
                      "paper_2408_08933_gb300/csrc/roar_knn.cu", "paper_2408_08933_gb300/csrc/roar_knn_tc.cu",
                      "paper_2408_08933_gb300/csrc/roar_search_kernel.cuh",
                      "paper_2408_08933_gb300/csrc/roar_search.cu"])
-    cache = os.path.join(CACHE_DIR, f"{w.name}_{w.n}_{w.n_train}_{w.n_test}_{key}.npz")
+    cache = os.path.join(CACHE_DIR, f"{w.name}_{w.n}_{w.n_train}_{w.n_test}_{w.offset_norm}_{w.noise}_{key}.npz")
     t0 = time.time()
     X = rs.base(w)
     Q = rs.test_queries(w)
@@ -310,9 +310,10 @@ def _time_once(fn, torch, reps=3):
 
 
 def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bstats, log):
-    """The precision (10M x 512), uneven (1M x 512) and serving (10M x 200) workloads."""
+    """The precision (10M x 512), uneven (1M x 512) and serving (10M x 200) workloads,
+    and the OOD-built against ID-built graph comparison (ood)."""
     nq = Q.shape[0]
-    res = {"mode": args.mode, "workload": w.name, "n": w.n, "d": w.d, "build": bstats}
+    res = {"mode": args.mode, "workload": w.name, "n": w.n, "d": w.d, "offset_norm": w.offset_norm, "build": bstats}
     forms = {}
     if args.mode == "precision":
         sweepL = [50, 75, 100, 150, 200, 300, 400, 500, 1024]
@@ -386,6 +387,46 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
                     "graph_captured": True})
         plan.close()
         idx.close()
+    elif args.mode == "ood":
+        # The paper's central comparison on synthetic data: a graph built from
+        # OOD training queries (RoarGraph as specified) against one built the
+        # same way from in-distribution training queries, searched with OOD
+        # and with ID test queries.
+        idq = rs.id_queries(w, w.n_train + nq)
+        Tid = torch.from_numpy(idq[:w.n_train]).to(dev)
+        Qid = torch.from_numpy(np.ascontiguousarray(idq[w.n_train:])).to(dev)
+        del idq
+        gi, _ = pkg.knn(Qid, Xd, 10)
+        torch.cuda.synchronize()
+        gt_id = gi.cpu().numpy().view(np.uint32)
+        t0 = time.time()
+        adj_id, entry_id, st_id = pkg.build_index(Xd, Tid, nq_depth=100, M=32, L_build=500)
+        torch.cuda.synchronize()
+        log(f"ID-built graph in {time.time() - t0:.1f}s")
+        del Tid
+        sweepL = [10, 20, 30, 50, 75, 100, 150, 200, 300, 500]
+        graphs = {"built_from_ood_queries": (adj, entry), "built_from_id_queries": (adj_id, entry_id)}
+        qsets = {"ood_queries": (Qd, gt), "id_queries": (Qid, gt_id)}
+        table = {}
+        for gname, (a_, e_) in graphs.items():
+            gidx = pkg.Index(Xd, a_, e_, max_visits=16384)
+            for qname, (Qs, gts) in qsets.items():
+                rows = {}
+                for L in sweepL:
+                    ms = _time_once(lambda: gidx.search(Qs, 10, L), torch)
+                    ids, dist, visits, hops, st = gidx.search(Qs, 10, L)
+                    torch.cuda.synchronize()
+                    rows[str(L)] = {"recall_at_10": _recall(ids.cpu().numpy().view(np.uint32), gts),
+                                    "visits": float(visits.double().mean()), "hops": float(hops.double().mean()),
+                                    "qps": Qs.shape[0] / (ms / 1e3)}
+                at = [L for L in sweepL if rows[str(L)]["recall_at_10"] >= TARGET_RECALL]
+                table[f"{gname}/{qname}"] = {
+                    "sweep": rows,
+                    "first_L_at_recall_0.90": at[0] if at else None,
+                    "visits_at_that_L": rows[str(at[0])]["visits"] if at else None}
+                log(f"{gname}/{qname}: {table[f'{gname}/{qname}']['first_L_at_recall_0.90']}")
+            gidx.close()
+        res.update({"graphs": table, "build_id_graph": st_id})
     elif args.mode == "serving":
         codes, sc = pkg.quantize(Xd, "bf16")
         sidx = pkg.Index(Xd, adj, entry, dtype="bf16", trav=codes, scales=None, max_visits=16384)
@@ -426,8 +467,11 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override base rows (smaller runs)")
     ap.add_argument("--n-train", type=int, default=0, help="override training queries")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving"],
-                    help="main: the benchmark line; others: the precision / uneven / serving workloads")
+    ap.add_argument("--offset-norm", type=float, default=0.0,
+                    help="override the OOD offset norm (ood mode experiments; the workloads use 1.5)")
+    ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving", "ood"],
+                    help="main: the benchmark line; others: the precision / uneven / serving workloads, "
+                         "and ood: OOD-built against ID-built graphs with OOD and ID queries")
     ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -459,6 +503,8 @@ def main():
         w = rs.scaled(w, n=args.n, n_train=args.n_train or min(args.n, w.n_train))
     elif args.n_train:
         w = rs.scaled(w, n_train=args.n_train)
+    if args.offset_norm > 0:
+        w = rs.scaled(w, offset_norm=args.offset_norm)
     dev, X, Q, Xd, Qd, adj, entry, gt, bstats = _setup(w, torch, pkg, rs, log)
     if args.mode != "main":
         out = _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bstats, log)
