@@ -427,6 +427,63 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
                 log(f"{gname}/{qname}: {table[f'{gname}/{qname}']['first_L_at_recall_0.90']}")
             gidx.close()
         res.update({"graphs": table, "build_id_graph": st_id})
+    elif args.mode == "ablation":
+        # Sec. 5.4: search the bipartite graph G_bi (base and training-query
+        # nodes), the projected graph G_pj and the final RoarGraph with the
+        # same OOD queries. G_bi: base x -> every training query whose nearest
+        # base row is x (at most 128 kept), query t -> its other N_q - 1
+        # nearest base rows; query nodes are searched like base rows and
+        # dropped from the answers.
+        t0 = time.time()
+        T = rs.train_queries(w)
+        Td = torch.from_numpy(T).to(dev)
+        del T
+        adj_f, entry_f, st_f, pj = pkg.build_index(Xd, Td, nq_depth=100, M=32, L_build=500, return_pj=True)
+        kid, _ = pkg.knn(Td, Xd, 100)
+        torch.cuda.synchronize()
+        knn_h = kid.cpu().numpy().view(np.uint32)
+        del kid
+        n, nt = w.n, Td.shape[0]
+        RB = 128
+        piv = knn_h[:, 0].astype(np.int64)
+        order = np.argsort(piv, kind="stable")
+        ps = piv[order]
+        start = np.searchsorted(ps, np.arange(n))
+        rank = np.arange(nt) - start[ps]
+        keep = rank < RB
+        adj_bi = np.full((n + nt, RB), 0xFFFFFFFF, dtype=np.uint32)
+        adj_bi[ps[keep], rank[keep]] = (n + order[keep]).astype(np.uint32)
+        adj_bi[n:, :knn_h.shape[1] - 1] = knn_h[:, 1:]
+        Xbi = torch.cat([Xd, Td])
+        del Td
+        adj_bi_d = torch.from_numpy(adj_bi.view(np.int32)).to(dev)
+        log(f"graphs ready in {time.time() - t0:.1f}s")
+        graphs = {"G_bi": (Xbi, adj_bi_d, True), "G_pj": (Xd, pj, False), "RoarGraph": (Xd, adj_f, False)}
+        table = {}
+        for gname, (Xg, ag, has_q) in graphs.items():
+            gidx = pkg.Index(Xg, ag, entry_f, max_visits=16384)
+            rows = {}
+            for L in (10, 20, 50, 100, 200, 500):
+                kq = L if has_q else 10
+                ms = _time_once(lambda: gidx.search(Qd, kq, L), torch)
+                ids, dist, visits, hops, st = gidx.search(Qd, kq, L)
+                torch.cuda.synchronize()
+                ih = ids.cpu().numpy().view(np.uint32)
+                if has_q:   # first 10 base ids of each answer
+                    base = np.full((ih.shape[0], 10), 0xFFFFFFFF, dtype=np.uint32)
+                    for i in range(ih.shape[0]):
+                        b = ih[i][ih[i] < n][:10]
+                        base[i, :len(b)] = b
+                    ih = base
+                rows[str(L)] = {"recall_at_10": _recall(ih, gt), "visits": float(visits.double().mean()),
+                                "hops": float(hops.double().mean()),
+                                "visits_per_hop": float(visits.double().mean() / max(hops.double().mean(), 1.0)),
+                                "qps": nq / (ms / 1e3)}
+            gidx.close()
+            table[gname] = rows
+            log(f"{gname}: {rows}")
+        res.update({"graphs": table, "g_bi_rows": int(n + nt), "g_bi_query_edges_capped": int((~keep).sum()),
+                    "build": st_f})
     elif args.mode == "serving":
         codes, sc = pkg.quantize(Xd, "bf16")
         sidx = pkg.Index(Xd, adj, entry, dtype="bf16", trav=codes, scales=None, max_visits=16384)
@@ -469,9 +526,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--offset-norm", type=float, default=0.0,
                     help="override the OOD offset norm (ood mode experiments; the workloads use 1.5)")
-    ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving", "ood"],
+    ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving", "ood", "ablation"],
                     help="main: the benchmark line; others: the precision / uneven / serving workloads, "
-                         "and ood: OOD-built against ID-built graphs with OOD and ID queries")
+                         "ood: OOD-built against ID-built graphs with OOD and ID queries, "
+                         "ablation: G_bi / G_pj / RoarGraph")
     ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -357,14 +357,18 @@ roar_status roar_acquire(const float *X, int64_t n, int32_t d, const uint32_t *x
  * Build a RoarGraph index (Alg. 1): training-query kNN on the GPU (roar_knn,
  * depth nq_depth = N_q), bipartite graph, neighbourhood-aware projection with
  * AcquireNeighbors (Alg. 2, Alg. 3) on host threads, connectivity
- * enhancement with beam searches of width L_build on the GPU, then
- * reachability repair. The host steps run in batched rounds (all pivots, then
- * all reverse edges), deterministic for any thread count.
+ * enhancement with beam searches of width L_build and its AcquireNeighbors
+ * pruning on the GPU (roar_search, roar_acquire), then reachability repair.
+ * The rounds are batched (all pivots, then all reverse edges; enhancement in
+ * chunks), deterministic for any thread count.
  *   X_dev [n][d], T_dev [nt][d]   device FP32 base rows and training queries.
  *   M                             out-degree bound of each phase; rows hold 2M.
  *   L_build                       candidate-set and beam size (M..ROAR_MAX_L).
  *   adj_dev                       device [n][2M] uint32 output, padded with
  *                                 ROAR_NONE_ID.
+ *   pj_dev                        NULL or device [n][M] uint32 output: the
+ *                                 projected graph G_pj before enhancement
+ *                                 (for ablations), padded with ROAR_NONE_ID.
  *   entry_out                     the medoid.
  *   stats                         NULL or double[16]: total, kNN, projection,
  *                                 enhancement-search, reverse/merge and repair
@@ -377,7 +381,8 @@ roar_status roar_acquire(const float *X, int64_t n, int32_t d, const uint32_t *x
  */
 roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const float *T_dev, int64_t nt,
                              int32_t nq_depth, int32_t M, int32_t L_build, int32_t threads,
-                             uint32_t *adj_dev, uint32_t *entry_out, double *stats, void *stream);
+                             uint32_t *adj_dev, uint32_t *pj_dev, uint32_t *entry_out, double *stats,
+                             void *stream);
 
 #ifdef __cplusplus
 }

@@ -94,7 +94,7 @@ def lib() -> ctypes.CDLL:
     L.roar_medoid.restype = ctypes.c_int
     L.roar_acquire.argtypes = [P, i64, i32, P, i64, P, i32, P, i32, i32, P, P, P, P]
     L.roar_acquire.restype = ctypes.c_int
-    L.roar_build_index.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P,
+    L.roar_build_index.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P, P,
                                    ctypes.POINTER(u32), P, P]
     L.roar_build_index.restype = ctypes.c_int
     _lib = L
@@ -235,9 +235,9 @@ def roar_medoid(X_host, n, d, threads=0):
     return e.value
 
 
-def roar_build_index(X, n, d, T, nt, nq_depth, M, L_build, threads, adj, stats, stream=None):
+def roar_build_index(X, n, d, T, nt, nq_depth, M, L_build, threads, adj, stats, stream=None, pj=None):
     e = ctypes.c_uint32()
-    _check(lib().roar_build_index(X, n, d, T, nt, nq_depth, M, L_build, threads, adj,
+    _check(lib().roar_build_index(X, n, d, T, nt, nq_depth, M, L_build, threads, adj, pj,
                                   ctypes.byref(e), stats, stream), "roar_build_index")
     return e.value
 
@@ -372,19 +372,23 @@ STAT_KEYS = ["total_s", "knn_s", "projection_s", "enhance_search_s", "reverse_me
              "unreachable_after_repair"]
 
 
-def build_index(X, T, nq_depth=100, M=32, L_build=500, threads=0, stream=None):
+def build_index(X, T, nq_depth=100, M=32, L_build=500, threads=0, stream=None, return_pj=False):
     """RoarGraph construction (Alg. 1) of CUDA float32 base rows X [n, d] from
-    training queries T [nt, d]. Returns (adj int32 [n, 2M] on X's device, entry, stats)."""
+    training queries T [nt, d]. Returns (adj int32 [n, 2M] on X's device, entry,
+    stats), and with return_pj also the projected graph G_pj (int32 [n, M])."""
     import numpy as np
     import torch
 
     assert X.is_cuda and T.is_cuda and X.dtype == torch.float32 and T.dtype == torch.float32
     n, d = X.shape
     adj = torch.empty((n, 2 * M), dtype=torch.int32, device=X.device)
+    pj = torch.empty((n, M), dtype=torch.int32, device=X.device) if return_pj else None
     st = np.zeros(16, dtype=np.float64)
     entry = roar_build_index(_ptr(X), n, d, _ptr(T), T.shape[0], nq_depth, M, L_build, threads,
-                             _ptr(adj), st.ctypes.data, _stream_ptr(stream))
-    return adj, entry, dict(zip(STAT_KEYS, st.tolist()))
+                             _ptr(adj), st.ctypes.data, _stream_ptr(stream),
+                             pj=_ptr(pj) if pj is not None else None)
+    stats = dict(zip(STAT_KEYS, st.tolist()))
+    return (adj, entry, stats, pj) if return_pj else (adj, entry, stats)
 
 
 def acquire(X, xs, cand, ncand, M, fill, sorted_out=False, stream=None):

@@ -428,7 +428,7 @@ extern "C" roar_status roar_medoid(const float *X_host, int64_t n, int32_t d, in
 
 extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const float *T_dev,
                                         int64_t nt, int32_t nq_depth, int32_t M, int32_t L_build,
-                                        int32_t threads, uint32_t *adj_dev, uint32_t *entry_out,
+                                        int32_t threads, uint32_t *adj_dev, uint32_t *pj_dev, uint32_t *entry_out,
                                         double *stats, void *stream) {
     if (!X_dev || !T_dev || !adj_dev || !entry_out || n < 2 || nt < 1 || d < 4 || d % 4 ||
         d > 1024 || nq_depth < 2 || nq_depth > 128 || nq_depth > n || M < 1 || 2 * M > ROAR_MAX_RMAX ||
@@ -547,6 +547,15 @@ extern "C" roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d
     build_log("projection done in %.1f s (%.0f pivots)", st[2], (double)pivots.load());
     int64_t pj_edges = 0;
     for (int64_t i = 0; i < n; ++i) pj_edges += pj.cnt[i];
+    if (pj_dev) {  // G_pj as it stands before enhancement
+        std::vector<uint32_t> pjrows((size_t)n * M, kNone);
+        parallel_for(n, threads, [&](int64_t x, int) {
+            std::copy(pj.row(x), pj.row(x) + pj.cnt[x], pjrows.data() + (size_t)x * M);
+        });
+        e = cudaMemcpyAsync(pj_dev, pjrows.data(), pjrows.size() * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "roar_build_index: G_pj output");
+    }
 
     // Alg. 1, enhancement loop: beam search of every base row (GPU), AcquireNeighbors
     // without fill, reverse edges. The rows are processed in chunks of
