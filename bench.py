@@ -455,13 +455,18 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
         adj_bi[ps[keep], rank[keep]] = (n + order[keep]).astype(np.uint32)
         adj_bi[n:, :knn_h.shape[1] - 1] = knn_h[:, 1:]
         Xbi = torch.cat([Xd, Td])
+        # The medoid is usually no pivot, so it has no out-edge in G_bi: start
+        # G_bi searches at the training-query node nearest to it instead.
+        qe, _ = pkg.knn(Xd[entry_f:entry_f + 1].contiguous(), Td, 1)
+        entry_bi = n + int(qe.cpu().numpy().view(np.uint32)[0, 0])
         del Td
         adj_bi_d = torch.from_numpy(adj_bi.view(np.int32)).to(dev)
         log(f"graphs ready in {time.time() - t0:.1f}s")
-        graphs = {"G_bi": (Xbi, adj_bi_d, True), "G_pj": (Xd, pj, False), "RoarGraph": (Xd, adj_f, False)}
+        graphs = {"G_bi": (Xbi, adj_bi_d, True, entry_bi), "G_pj": (Xd, pj, False, entry_f),
+                  "RoarGraph": (Xd, adj_f, False, entry_f)}
         table = {}
-        for gname, (Xg, ag, has_q) in graphs.items():
-            gidx = pkg.Index(Xg, ag, entry_f, max_visits=16384)
+        for gname, (Xg, ag, has_q, eg) in graphs.items():
+            gidx = pkg.Index(Xg, ag, eg, max_visits=16384)
             rows = {}
             for L in (10, 20, 50, 100, 200, 500):
                 kq = L if has_q else 10
