@@ -74,6 +74,9 @@ def _load():
         lib.orc_beam_search.argtypes = [i32, P, P, P, i64, i32, P, i32, u32, P, i64, i32, i32, u32,
                                         P, P, P, P, P]
         lib.orc_beam_search.restype = ctypes.c_int
+        lib.orc_beam_search_tomb.argtypes = [i32, P, P, P, i64, i32, P, i32, u32, P, i64, i32, i32, u32,
+                                             P, P, P, P, P, P]
+        lib.orc_beam_search_tomb.restype = ctypes.c_int
         lib.orc_beam_search_trace.argtypes = [P, i64, i32, P, i32, u32, P, i32, u32, P, P, P, P, i64,
                                               P, P]
         lib.orc_beam_search_trace.restype = ctypes.c_int
@@ -210,13 +213,24 @@ def build_index(X, knn_ids, M: int, L: int, entry: int):
     return adj, pj, dict(zip(keys, (int(s) for s in stats)))
 
 
+def pack_tombstones(deleted) -> np.ndarray:
+    """Bitmap (uint32 words, bit id & 31 of word id >> 5) of a boolean mask."""
+    deleted = np.asarray(deleted, dtype=bool)
+    words = np.zeros((deleted.size + 31) // 32, dtype=np.uint32)
+    idx = np.nonzero(deleted)[0]
+    np.bitwise_or.at(words, idx >> 5, (np.uint32(1) << (idx & 31).astype(np.uint32)))
+    return words
+
+
 def beam_search(X32, adj, entry: int, Q, k: int, L: int, max_visits: int = 1 << 20,
-                dtype: str = "f32", Xt=None, scales=None):
+                dtype: str = "f32", Xt=None, scales=None, tomb=None):
     """Beam search (Sec. 4.3) for every row of Q.
 
     dtype "f32": traversal and result on X32. "bf16" / "fp8": traversal on the
     quantised copy ``Xt`` (uint16 / uint8 codes, FP8 with per-row ``scales``),
-    then the whole final pool is re-ranked with FP32 distances.
+    then the whole final pool is re-ranked with FP32 distances. ``tomb``: None
+    or a deletion bitmap (pack_tombstones); deleted rows route but are not
+    answers (Sec. 5.7).
     Returns ids [nq][k] (uint32), dist [nq][k] (float32), visits, hops, status.
     """
     X32 = _f32(X32)
@@ -236,9 +250,10 @@ def beam_search(X32, adj, entry: int, Q, k: int, L: int, max_visits: int = 1 << 
     visits = np.empty(nq, dtype=np.uint32)
     hops = np.empty(nq, dtype=np.uint32)
     status = np.empty(nq, dtype=np.int32)
-    rc = _load().orc_beam_search(code, _p(Xt_arr), _p(sc), _p(X32), n, d, _p(adj), adj.shape[1],
-                                 entry, _p(Q), nq, k, L, max_visits, _p(ids), _p(dist), _p(visits),
-                                 _p(hops), _p(status))
+    tw = None if tomb is None else np.ascontiguousarray(tomb, dtype=np.uint32)
+    rc = _load().orc_beam_search_tomb(code, _p(Xt_arr), _p(sc), _p(X32), n, d, _p(adj), adj.shape[1],
+                                      entry, _p(Q), nq, k, L, max_visits, _p(tw), _p(ids), _p(dist),
+                                      _p(visits), _p(hops), _p(status))
     if rc != 0:
         raise ValueError(f"orc_beam_search failed: {rc}")
     return ids, dist, visits, hops, status

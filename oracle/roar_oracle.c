@@ -286,11 +286,18 @@ static int check_graph_args(int64_t n, int32_t d, int32_t rmax, uint32_t entry, 
  * Returns 0, or 1 for bad arguments, 2 when out of memory. Per-query status
  * (0, or 4 when the visit cap ended the search) goes to qstatus.
  */
-int orc_beam_search(int32_t dtype, const void *Xt, const float *scales, const float *X32,
-                    int64_t n, int32_t d, const uint32_t *adj, int32_t rmax, uint32_t entry,
-                    const float *Q, int64_t nq, int32_t k, int32_t L, uint32_t max_visits,
-                    uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops,
-                    int32_t *qstatus) {
+/*
+ * Tombstones (deletion, Sec. 5.7): `tomb` is NULL or a bitmap of n bits (bit
+ * id & 31 of word id >> 5) marking deleted rows. Deleted rows are searched
+ * through like any other (the traversal, visits and hops do not change) but
+ * are left out of the answer: the result is the first k entries of the final
+ * (re-ranked) pool whose ids are not deleted.
+ */
+int orc_beam_search_tomb(int32_t dtype, const void *Xt, const float *scales, const float *X32,
+                         int64_t n, int32_t d, const uint32_t *adj, int32_t rmax, uint32_t entry,
+                         const float *Q, int64_t nq, int32_t k, int32_t L, uint32_t max_visits,
+                         const uint32_t *tomb, uint32_t *ids, float *dist, uint32_t *visits,
+                         uint32_t *hops, int32_t *qstatus) {
     if (check_graph_args(n, d, rmax, entry, k, L) || nq < 0 || dtype < 0 || dtype > 2)
         return ORC_EINVAL;
     if (dtype != 0 && X32 == NULL) return ORC_EINVAL;
@@ -318,9 +325,17 @@ int orc_beam_search(int32_t dtype, const void *Xt, const float *scales, const fl
                 pool[j] = e;
             }
         }
-        for (int32_t r = 0; r < k; ++r) {
-            ids[qi * k + r] = r < size ? pool[r].id : ORC_NONE;
-            dist[qi * k + r] = r < size ? pool[r].d : INFINITY;
+        int32_t r = 0;
+        for (int32_t i = 0; i < size && r < k; ++i) {
+            const uint32_t u = pool[i].id;
+            if (tomb && ((tomb[u >> 5] >> (u & 31)) & 1u)) continue;   /* deleted: not an answer */
+            ids[qi * k + r] = u;
+            dist[qi * k + r] = pool[i].d;
+            ++r;
+        }
+        for (; r < k; ++r) {
+            ids[qi * k + r] = ORC_NONE;
+            dist[qi * k + r] = INFINITY;
         }
         if (visits) visits[qi] = nv;
         if (hops) hops[qi] = nh;
@@ -330,6 +345,15 @@ int orc_beam_search(int32_t dtype, const void *Xt, const float *scales, const fl
     free(visited);
     free(tmp);
     return ORC_OK;
+}
+
+int orc_beam_search(int32_t dtype, const void *Xt, const float *scales, const float *X32,
+                    int64_t n, int32_t d, const uint32_t *adj, int32_t rmax, uint32_t entry,
+                    const float *Q, int64_t nq, int32_t k, int32_t L, uint32_t max_visits,
+                    uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops,
+                    int32_t *qstatus) {
+    return orc_beam_search_tomb(dtype, Xt, scales, X32, n, d, adj, rmax, entry, Q, nq, k, L, max_visits,
+                                NULL, ids, dist, visits, hops, qstatus);
 }
 
 /* Single FP32 query with its expansion order (for hand-traced tests). */

@@ -82,3 +82,34 @@ def test_rejects_bad_arguments():
         oracle.beam_search(X, adj, 5, q, 1, 1)       # entry out of range
     with pytest.raises(ValueError):
         oracle.beam_search(X, adj, 0, q, 3, 2)       # k > L
+
+
+def test_tombstones_hand_traced_path_graph():
+    """Deleted rows route but are not answers (Sec. 5.7), on the hand-traced graph."""
+    g = load_golden("beam_path6_tomb.json")
+    X, adj = path_graph(g["a"])
+    q = np.array([[1, 0, 0, 0]], dtype=np.float32)
+    for c in g["cases"]:
+        deleted = np.zeros(len(g["a"]), dtype=bool)
+        deleted[c["deleted"]] = True
+        ids, dist, visits, hops, st = oracle.beam_search(X, adj, g["entry"], q, c["k"], c["L"],
+                                                         tomb=oracle.pack_tombstones(deleted))
+        assert ids[0].tolist() == c["ids"], c
+        assert dist[0].tolist() == [float(v) for v in c["dist"]], c
+        assert (int(visits[0]), int(hops[0])) == (c["visits"], c["hops"]), c
+
+
+def test_tombstones_filter_the_same_traversal(tiny):
+    """With tombstones the visits and hops are unchanged and the answers are the
+    untombstoned search's final pool with the deleted ids removed."""
+    rng = np.random.default_rng(3)
+    deleted = rng.random(tiny["X"].shape[0]) < 0.2
+    Q = tiny["Q"][:64]
+    L = 50
+    full = oracle.beam_search(tiny["X"], tiny["adj"], tiny["entry"], Q, L, L)
+    got = oracle.beam_search(tiny["X"], tiny["adj"], tiny["entry"], Q, 10, L,
+                             tomb=oracle.pack_tombstones(deleted))
+    assert np.array_equal(full[2], got[2]) and np.array_equal(full[3], got[3])
+    for i in range(Q.shape[0]):
+        alive = [u for u in full[0][i].tolist() if u != 0xFFFFFFFF and not deleted[u]][:10]
+        assert got[0][i].tolist() == alive + [0xFFFFFFFF] * (10 - len(alive))
