@@ -113,6 +113,21 @@ void roar_index_destroy(roar_index *idx);
 roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2);
 
 /*
+ * Deletion by tombstones (Sec. 5.7): deleted rows still take part in routing
+ * (they are visited and expanded like any other) but are left out of the
+ * answers, which are the first k live entries of the final pool (after the
+ * FP32 re-rank for the reduced-precision forms).
+ *   bits  device bitmap of ceil(n/32) uint32 words, bit (id & 31) of word
+ *         (id >> 5) set for a deleted row; NULL clears the tombstones. The
+ *         caller owns it and may change its contents between searches; the
+ *         handle keeps the pointer. Searches, uneven batches and servers
+ *         created after this call read it; a captured plan keeps the pointer
+ *         it was created with.
+ * Errors: ROAR_EINVAL.
+ */
+roar_status roar_index_set_tombstones(roar_index *idx, const uint32_t *bits);
+
+/*
  * Beam search (Sec. 4.3) of nq queries, each owned by one warp: start from
  * the entry, repeatedly expand the closest unexpanded pool entry, score its
  * unvisited out-neighbours, keep the first L under (distance, id), stop when

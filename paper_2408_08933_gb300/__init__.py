@@ -55,6 +55,8 @@ def lib() -> ctypes.CDLL:
     L.roar_index_create.restype = ctypes.c_int
     L.roar_index_set_hash_log2.argtypes = [P, i32]
     L.roar_index_set_hash_log2.restype = ctypes.c_int
+    L.roar_index_set_tombstones.argtypes = [P, P]
+    L.roar_index_set_tombstones.restype = ctypes.c_int
     L.roar_index_destroy.argtypes = [P]
     L.roar_index_destroy.restype = None
     L.roar_search.argtypes = [P, P, i64, i32, i32, P, P, P, P, P, P]
@@ -113,6 +115,10 @@ def roar_index_create(n, d, base_f32, trav_dtype, base_trav, scales, adj, rmax, 
     _check(lib().roar_index_create(n, d, base_f32, trav_dtype, base_trav, scales, adj, rmax,
                                    entry, max_visits, ctypes.byref(h)), "roar_index_create")
     return h.value
+
+
+def roar_index_set_tombstones(idx, bits):
+    _check(lib().roar_index_set_tombstones(idx, bits), "roar_index_set_tombstones")
 
 
 def roar_index_set_hash_log2(handle, log2):
@@ -277,6 +283,12 @@ class Index:
 
     def set_hash_log2(self, log2: int):
         roar_index_set_hash_log2(self.handle, log2)
+
+    def set_tombstones(self, bits):
+        """Deletion bitmap (CUDA int32 [ceil(n/32)] words, bit id & 31 of word
+        id >> 5), or None to clear. The tensor is kept alive with the index."""
+        self._tomb = bits
+        roar_index_set_tombstones(self.handle, _ptr(bits) if bits is not None else None)
 
     def close(self):
         if getattr(self, "handle", None):

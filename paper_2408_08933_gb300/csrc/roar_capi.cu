@@ -42,6 +42,7 @@ struct roar_index {
     const void *trav;
     const float *scales;
     const uint32_t *adj;
+    const uint32_t *tomb = nullptr;  // caller-owned deletion bitmap or null
     int32_t rmax;
     uint32_t entry;
     uint32_t max_visits;
@@ -163,6 +164,16 @@ extern "C" roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2) {
     return ROAR_OK;
 }
 
+extern "C" roar_status roar_index_set_tombstones(roar_index *idx, const uint32_t *bits) {
+    if (!idx || (bits && !aligned(bits, 4))) {
+        set_error("roar_index_set_tombstones: bad handle or bitmap pointer");
+        return ROAR_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->mu);
+    idx->tomb = bits;
+    return ROAR_OK;
+}
+
 extern "C" void roar_index_destroy(roar_index *idx) {
     if (!idx) return;
     cudaDeviceSynchronize();
@@ -217,6 +228,7 @@ roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &block
     a.scales = idx->scales;
     a.base32 = idx->base32;
     a.adj = idx->adj;
+    a.tomb = idx->tomb;
     a.n = idx->n;
     a.d = idx->d;
     a.rmax = idx->rmax;

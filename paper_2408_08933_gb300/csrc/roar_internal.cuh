@@ -40,6 +40,7 @@ struct SearchArgs {
     const float *scales;     // FP8 per-row scales [n] or null
     const float *base32;     // FP32 rows [n][d] (re-rank)
     const uint32_t *adj;     // [n][rmax]
+    const uint32_t *tomb;    // deletion bitmap [ceil(n/32)] or null: deleted rows route, are not answers
     int64_t n;
     int32_t d;
     int32_t rmax;

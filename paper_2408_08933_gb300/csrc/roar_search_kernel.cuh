@@ -738,14 +738,28 @@ beam_search_kernel(const SearchArgs a) {
         }
 
         // Output (re-ranked in FP32, in place, for the reduced-precision forms).
+        // Deleted rows (tombstones) took part in routing and are skipped here.
         const int fsize = ctl[2];
+        auto deleted = [&](uint32_t u) -> bool { return (__ldcg(a.tomb + (u >> 5)) >> (u & 31)) & 1u; };
         if constexpr (DT != 0) {
             score_rows<0, NCH, B0>(a.base32, nullptr, d, d4, qr, pi, fsize, pd, lane, wt * B0, TW * B0);
             tsync();
             if (leader) {
+                int alive = fsize;
+                if (a.tomb) {  // a deleted entry ranks after every live one and is not written
+                    alive = 0;
+                    for (int b0 = 0; b0 < fsize; b0 += 32) {
+                        const int i = b0 + lane;
+                        const bool dead = i < fsize && deleted(pi[i] & kIdMask);
+                        if (dead) pd[i] = __int_as_float(0x7f800000);
+                        alive += __popc(__ballot_sync(kFull, i < fsize && !dead));
+                    }
+                    __syncwarp();
+                }
                 for (int i = lane; i < fsize; i += 32) {
                     const float di = pd[i];
                     const uint32_t ii = pi[i] & kIdMask;
+                    if (a.tomb && deleted(ii)) continue;
                     int r = 0;
                     for (int x = 0; x < fsize && r < k; ++x)
                         r += less_entry(pd[x], pi[x] & kIdMask, di, ii) ? 1 : 0;
@@ -754,16 +768,36 @@ beam_search_kernel(const SearchArgs a) {
                         a.dist[ooff + r] = di;
                     }
                 }
-                for (int r = fsize + lane; r < k; r += 32) {
+                for (int r = alive + lane; r < k; r += 32) {
                     a.ids[ooff + r] = kNone;
                     a.dist[ooff + r] = __int_as_float(0x7f800000);
                 }
             }
         } else if (leader) {
-            for (int r = lane; r < k; r += 32) {
-                const bool have = r < fsize;
-                a.ids[ooff + r] = have ? (pi[r] & kIdMask) : kNone;
-                a.dist[ooff + r] = have ? pd[r] : __int_as_float(0x7f800000);
+            if (!a.tomb) {
+                for (int r = lane; r < k; r += 32) {
+                    const bool have = r < fsize;
+                    a.ids[ooff + r] = have ? (pi[r] & kIdMask) : kNone;
+                    a.dist[ooff + r] = have ? pd[r] : __int_as_float(0x7f800000);
+                }
+            } else {  // the first k live pool entries, in pool order
+                int r = 0;
+                for (int b0 = 0; b0 < fsize && r < k; b0 += 32) {
+                    const int i = b0 + lane;
+                    const uint32_t u = i < fsize ? (pi[i] & kIdMask) : 0u;
+                    const bool live = i < fsize && !deleted(u);
+                    const unsigned m = __ballot_sync(kFull, live);
+                    const int p = r + __popc(m & ((1u << lane) - 1u));
+                    if (live && p < k) {
+                        a.ids[ooff + p] = u;
+                        a.dist[ooff + p] = pd[i];
+                    }
+                    r += __popc(m);
+                }
+                for (int p = min(r, k) + lane; p < k; p += 32) {
+                    a.ids[ooff + p] = kNone;
+                    a.dist[ooff + p] = __int_as_float(0x7f800000);
+                }
             }
         }
         if (leader) {
