@@ -88,6 +88,8 @@ def _load():
         lib.orc_acquire_neighbors.restype = i32
         lib.orc_acquire_neighbors_f32.argtypes = [P, i64, i32, u32, P, i32, i32, i32, P]
         lib.orc_acquire_neighbors_f32.restype = i32
+        lib.orc_insert.argtypes = [P, i64, i32, P, i32, u32, i64, P, i64, P, P, P, i32, i32, i32, P]
+        lib.orc_insert.restype = i32
         lib.orc_build.argtypes = [P, i64, i64, i32, P, i32, i32, i32, u32, P, P, P]
         lib.orc_build.restype = ctypes.c_int
         _lib = lib
@@ -192,6 +194,26 @@ def acquire_neighbors_f32(X, x: int, cand, M: int, fill: bool):
     if r < 0:
         raise ValueError("orc_acquire_neighbors_f32: bad arguments")
     return res[:r].copy()
+
+
+def insert(X, adj, entry: int, n_old: int, T, pivot, nout, nout_cnt, M: int, L: int):
+    """Insertion through the saved bipartite graph (Sec. 5.7) of rows n_old..n-1
+    of X into the graph adj [n][R] (rows >= n_old empty). pivot [nt]: each
+    training query's nearest base row; nout [nt][cap] / nout_cnt [nt]: N_out
+    lists. Returns (adj, nout, nout_cnt, chosen_q) updated copies."""
+    X = _f32(X)
+    T = _f32(T)
+    adj = np.ascontiguousarray(adj, dtype=np.uint32).copy()
+    nout = np.ascontiguousarray(nout, dtype=np.uint32).copy()
+    nout_cnt = np.ascontiguousarray(nout_cnt, dtype=np.int32).copy()
+    pivot = np.ascontiguousarray(pivot, dtype=np.uint32)
+    n, d = X.shape
+    chosen = np.full(n - n_old, -1, dtype=np.int32)
+    rc = _load().orc_insert(_p(X), n, d, _p(adj), adj.shape[1], entry, n_old, _p(T), T.shape[0], _p(pivot),
+                            _p(nout), _p(nout_cnt), nout.shape[1], M, L, _p(chosen))
+    if rc != 0:
+        raise ValueError(f"orc_insert failed: {rc}")
+    return adj, nout, nout_cnt, chosen
 
 
 def build_index(X, knn_ids, M: int, L: int, entry: int):

@@ -851,3 +851,123 @@ done:
     free(queue);
     return rc;
 }
+
+
+/*
+ * Insertion through the saved bipartite graph (Sec. 5.7), one new row at a
+ * time in id order (rows n_old .. n_total-1 of X; their adjacency rows start
+ * empty and nothing links to them, so searches cannot reach them before
+ * their turn). For new row v:
+ *   1. beam search (FP32, width L) of X[v] from the entry over the current
+ *      graph;
+ *   2. the first pool entry b that some training query is connected to (b is
+ *      in N_out(t), or b is the nearest base row (pivot) of t);
+ *   3. of those queries, q = the one nearest to v (-dot_fixed, ties by id);
+ *   4. projection of the sub-bipartite graph N_out(q) + q + v with v as the
+ *      pivot: N(v) = Alg. 3 with fill (FP32 fixed-order distances) over
+ *      N_out(q) sorted by (delta(v, c), id); when no pool entry is connected
+ *      to a query, over the search pool instead;
+ *   5. the edges of v merge into the graph: v's row is N(v); each p in N(v)
+ *      gets p -> v, appended when its row has room, else its row and v are
+ *      re-pruned to R with Alg. 3 (fill) in (delta(p, c), id) order;
+ *   6. v joins N_out(q) (while N_out(q) has room) for later insertions.
+ * adj [n_total][R] and nout [nt][nout_cap] / nout_cnt [nt] are updated in
+ * place; chosen_q[i] is q for row n_old + i, or -1. Returns 0, 1 for bad
+ * arguments, 2 when out of memory.
+ */
+static void sort_by_fixed_dist(const float *X, int32_t d, const float *xv, uint32_t *ids, int32_t m) {
+    for (int32_t i = 1; i < m; ++i) {
+        const uint32_t e = ids[i];
+        const float de = -orc_dot_fixed(xv, X + (int64_t)e * d, d);
+        int32_t j = i;
+        while (j > 0) {
+            const float dj = -orc_dot_fixed(xv, X + (int64_t)ids[j - 1] * d, d);
+            if (!less_f32(de, e, dj, ids[j - 1])) break;
+            ids[j] = ids[j - 1];
+            --j;
+        }
+        ids[j] = e;
+    }
+}
+
+int orc_insert(const float *X, int64_t n_total, int32_t d, uint32_t *adj, int32_t R, uint32_t entry,
+               int64_t n_old, const float *T, int64_t nt, const uint32_t *pivot, uint32_t *nout,
+               int32_t *nout_cnt, int32_t nout_cap, int32_t M, int32_t L, int32_t *chosen_q) {
+    if (n_old < 1 || n_total < n_old || (int64_t)entry >= n_old || d < 1 || R < 1 || M < 1 || M > R ||
+        L < 1 || nt < 1 || nout_cap < 1)
+        return ORC_EINVAL;
+    /* queries connected to each base row: in-edges from N_out, and pivot edges */
+    ulist *inc = (ulist *)calloc((size_t)n_total, sizeof(ulist));
+    ent32 *pool = (ent32 *)malloc(sizeof(ent32) * (size_t)L);
+    unsigned char *visited = (unsigned char *)malloc((size_t)n_total);
+    float *tmp = (float *)malloc(sizeof(float) * (size_t)d);
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nout_cap + L + R + 1));
+    uint32_t *res = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(R + 1));
+    int rc = ORC_OK;
+    if (!inc || !pool || !visited || !tmp || !cand || !res) { rc = ORC_ENOMEM; goto done; }
+    for (int64_t t = 0; t < nt; ++t) {
+        if (pivot[t] < n_total && ul_push(&inc[pivot[t]], (uint32_t)t)) { rc = ORC_ENOMEM; goto done; }
+        for (int32_t j = 0; j < nout_cnt[t]; ++j) {
+            const uint32_t b = nout[t * nout_cap + j];
+            if (b < n_total && !ul_has(&inc[b], (uint32_t)t) && ul_push(&inc[b], (uint32_t)t)) {
+                rc = ORC_ENOMEM;
+                goto done;
+            }
+        }
+    }
+    for (int64_t v = n_old; v < n_total; ++v) {
+        const float *xv = X + v * d;
+        int32_t size = 0;
+        uint32_t nv = 0, nh = 0;
+        search_one(0, X, NULL, n_total, d, adj, R, entry, xv, L, 1u << 20, pool, &size, &nv, &nh, NULL, 0,
+                   visited, tmp);
+        int64_t q = -1;
+        for (int32_t r = 0; r < size && q < 0; ++r) {
+            const ulist *qs = &inc[pool[r].id];
+            for (int32_t j = 0; j < qs->n; ++j) {
+                const uint32_t t = qs->v[j];
+                const float dt = -orc_dot_fixed(xv, T + (int64_t)t * d, d);
+                if (q < 0 || less_f32(dt, t, -orc_dot_fixed(xv, T + q * d, d), (uint32_t)q)) q = t;
+            }
+        }
+        int32_t nc = 0;
+        if (q >= 0) {
+            for (int32_t j = 0; j < nout_cnt[q]; ++j) cand[nc++] = nout[q * nout_cap + j];
+            sort_by_fixed_dist(X, d, xv, cand, nc);
+        } else {
+            for (int32_t r = 0; r < size; ++r) cand[nc++] = pool[r].id;   /* already in (delta, id) order */
+        }
+        int32_t nr = orc_acquire_neighbors_f32(X, n_total, d, (uint32_t)v, cand, nc, M, 1, res);
+        if (nr < 0) { rc = ORC_EINVAL; goto done; }
+        uint32_t *rowv = adj + v * R;
+        for (int32_t j = 0; j < R; ++j) rowv[j] = j < nr ? res[j] : ORC_NONE;
+        for (int32_t j = 0; j < nr; ++j) {
+            const uint32_t p = rowv[j];
+            uint32_t *rp = adj + (int64_t)p * R;
+            int32_t deg = 0, has = 0;
+            while (deg < R && rp[deg] != ORC_NONE) { has |= rp[deg] == (uint32_t)v; ++deg; }
+            if (has) continue;
+            if (deg < R) { rp[deg] = (uint32_t)v; continue; }
+            int32_t m = 0;
+            for (int32_t t = 0; t < R; ++t) cand[m++] = rp[t];
+            cand[m++] = (uint32_t)v;
+            sort_by_fixed_dist(X, d, X + (int64_t)p * d, cand, m);
+            const int32_t k2 = orc_acquire_neighbors_f32(X, n_total, d, p, cand, m, R, 1, res);
+            for (int32_t t = 0; t < R; ++t) rp[t] = t < k2 ? res[t] : ORC_NONE;
+        }
+        if (q >= 0 && nout_cnt[q] < nout_cap) {
+            nout[q * nout_cap + nout_cnt[q]++] = (uint32_t)v;
+            if (ul_push(&inc[v], (uint32_t)q)) { rc = ORC_ENOMEM; goto done; }
+        }
+        chosen_q[v - n_old] = (int32_t)q;
+    }
+done:
+    if (inc) for (int64_t i = 0; i < n_total; ++i) free(inc[i].v);
+    free(inc);
+    free(pool);
+    free(visited);
+    free(tmp);
+    free(cand);
+    free(res);
+    return rc;
+}
