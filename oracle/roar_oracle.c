@@ -858,8 +858,8 @@ done:
  * time in id order (rows n_old .. n_total-1 of X; their adjacency rows start
  * empty and nothing links to them, so searches cannot reach them before
  * their turn). For new row v:
- *   1. beam search (FP32, width L) of X[v] from the entry over the current
- *      graph;
+ *   1. beam search (FP32, width L, visit cap 16384) of X[v] from the entry
+ *      over the current graph;
  *   2. the first pool entry b that some training query is connected to (b is
  *      in N_out(t), or b is the nearest base row (pivot) of t);
  *   3. of those queries, q = the one nearest to v (-dot_fixed, ties by id);
@@ -919,7 +919,7 @@ int orc_insert(const float *X, int64_t n_total, int32_t d, uint32_t *adj, int32_
         const float *xv = X + v * d;
         int32_t size = 0;
         uint32_t nv = 0, nh = 0;
-        search_one(0, X, NULL, n_total, d, adj, R, entry, xv, L, 1u << 20, pool, &size, &nv, &nh, NULL, 0,
+        search_one(0, X, NULL, n_total, d, adj, R, entry, xv, L, 16384u, pool, &size, &nv, &nh, NULL, 0,
                    visited, tmp);
         int64_t q = -1;
         for (int32_t r = 0; r < size && q < 0; ++r) {

@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
     L.roar_medoid.restype = ctypes.c_int
     L.roar_acquire.argtypes = [P, i64, i32, P, i64, P, i32, P, i32, i32, P, P, P, P]
     L.roar_acquire.restype = ctypes.c_int
+    L.roar_insert.argtypes = [P, i64, i32, P, i32, u32, i64, P, i64, P, P, P, i32, i32, i32, P, P]
+    L.roar_insert.restype = ctypes.c_int
     L.roar_build_index.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P, P,
                                    ctypes.POINTER(u32), P, P]
     L.roar_build_index.restype = ctypes.c_int
@@ -401,6 +403,25 @@ def build_index(X, T, nq_depth=100, M=32, L_build=500, threads=0, stream=None, r
                              pj=_ptr(pj) if pj is not None else None)
     stats = dict(zip(STAT_KEYS, st.tolist()))
     return (adj, entry, stats, pj) if return_pj else (adj, entry, stats)
+
+
+def insert(X, adj, entry, n_old, T, pivot, nout, nout_cnt, M, L, stream=None):
+    """Insert rows n_old.. of CUDA X [n, d] into the CUDA graph adj [n, R]
+    (int32, rows >= n_old all -1) through the saved bipartite graph (Sec. 5.7).
+    T: host float32 [nt, d]; pivot: host uint32 [nt]; nout: host uint32
+    [nt, cap] and nout_cnt: host int32 [nt], updated in place. Returns the
+    chosen query per new row (numpy int32, -1 when none)."""
+    import numpy as np
+
+    n, d = X.shape
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    pivot = np.ascontiguousarray(pivot, dtype=np.uint32)
+    assert nout.dtype == np.uint32 and nout.flags.c_contiguous and nout_cnt.dtype == np.int32
+    chosen = np.full(n - n_old, -1, dtype=np.int32)
+    _check(lib().roar_insert(_ptr(X), n, d, _ptr(adj), adj.shape[1], entry, n_old, T.ctypes.data, T.shape[0],
+                             pivot.ctypes.data, nout.ctypes.data, nout_cnt.ctypes.data, nout.shape[1], M, L,
+                             chosen.ctypes.data, _stream_ptr(stream)), "roar_insert")
+    return chosen
 
 
 def acquire(X, xs, cand, ncand, M, fill, sorted_out=False, stream=None):
