@@ -489,6 +489,70 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
             log(f"{gname}: {rows}")
         res.update({"graphs": table, "g_bi_rows": int(n + nt), "g_bi_query_edges_capped": int((~keep).sum()),
                     "build": st_f})
+    elif args.mode == "update":
+        # Sec. 5.7: insertion through the saved bipartite graph, and deletion by
+        # tombstones. Build on the first 90 % of the rows, insert the rest,
+        # compare with the index built over all rows (the cached one).
+        n = w.n
+        n_old = n - n // 10
+        T = rs.train_queries(w)
+        Td = torch.from_numpy(T).to(dev)
+        t0 = time.time()
+        adj_old, entry_old, st_old = pkg.build_index(Xd[:n_old], Td, nq_depth=100, M=32, L_build=500)
+        kid, _ = pkg.knn(Td, Xd[:n_old], 100)
+        torch.cuda.synchronize()
+        build_s = time.time() - t0
+        knn_h = kid.cpu().numpy().view(np.uint32)
+        del kid, Td
+        cap = 99 + 64
+        nout = np.full((T.shape[0], cap), 0xFFFFFFFF, dtype=np.uint32)
+        nout[:, :99] = knn_h[:, 1:]
+        cnt = np.full(T.shape[0], 99, dtype=np.int32)
+        R = adj_old.shape[1]
+        adj_u = torch.full((n, R), -1, dtype=torch.int32, device=dev)
+        adj_u[:n_old] = adj_old
+        t0 = time.time()
+        chosen = pkg.insert(Xd, adj_u, entry_old, n_old, T, knn_h[:, 0], nout, cnt, 32, 100)
+        torch.cuda.synchronize()
+        ins_s = time.time() - t0
+        log(f"inserted {n - n_old} rows in {ins_s:.1f}s")
+        del T
+        table = {}
+        for gname, (a_, e_) in {"updated": (adj_u, entry_old), "rebuilt": (adj, entry)}.items():
+            gidx = pkg.Index(Xd, a_, e_, max_visits=16384)
+            rows = {}
+            for L in (50, 90, 100, 150, 200, 300):
+                ms = _time_once(lambda: gidx.search(Qd, 10, L), torch)
+                ids, dist, visits, hops, st = gidx.search(Qd, 10, L)
+                torch.cuda.synchronize()
+                rows[str(L)] = {"recall_at_10": _recall(ids.cpu().numpy().view(np.uint32), gt),
+                                "visits": float(visits.double().mean()), "qps": nq / (ms / 1e3)}
+            table[gname] = rows
+            gidx.close()
+        # deletion: 10 % of the rows tombstoned; ground truth over the live rows
+        dead = np.random.default_rng(5).random(n) < 0.1
+        words = np.zeros((n + 31) // 32, dtype=np.uint32)
+        di = np.nonzero(dead)[0]
+        np.bitwise_or.at(words, di >> 5, (np.uint32(1) << (di & 31).astype(np.uint32)))
+        g40, _ = pkg.knn(Qd, Xd, 40)
+        torch.cuda.synchronize()
+        g40 = g40.cpu().numpy().view(np.uint32)
+        gt_live = np.array([[u for u in row if not dead[u]][:10] for row in g40], dtype=np.uint32)
+        gidx = pkg.Index(Xd, adj_u, entry_old, max_visits=16384)
+        gidx.set_tombstones(torch.from_numpy(words.view(np.int32)).to(dev))
+        trows = {}
+        for L in (90, 100, 150):
+            ms = _time_once(lambda: gidx.search(Qd, 10, L), torch)
+            ids, *_ = gidx.search(Qd, 10, L)
+            torch.cuda.synchronize()
+            ih = ids.cpu().numpy().view(np.uint32)
+            trows[str(L)] = {"recall_at_10_live": _recall(ih, gt_live), "qps": nq / (ms / 1e3),
+                             "deleted_in_answers": int(dead[ih[ih != 0xFFFFFFFF]].sum())}
+        gidx.close()
+        res.update({"n_old": int(n_old), "inserted": int(n - n_old), "build_old_s": build_s,
+                    "insert_s": ins_s, "inserts_per_s": (n - n_old) / ins_s,
+                    "rows_with_a_connected_query": float((chosen >= 0).mean()),
+                    "search": table, "tombstones_10pct": trows})
     elif args.mode == "serving":
         codes, sc = pkg.quantize(Xd, "bf16")
         sidx = pkg.Index(Xd, adj, entry, dtype="bf16", trav=codes, scales=None, max_visits=16384)
@@ -531,10 +595,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--offset-norm", type=float, default=0.0,
                     help="override the OOD offset norm (ood mode experiments; the workloads use 1.5)")
-    ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving", "ood", "ablation"],
+    ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving", "ood", "ablation", "update"],
                     help="main: the benchmark line; others: the precision / uneven / serving workloads, "
                          "ood: OOD-built against ID-built graphs with OOD and ID queries, "
-                         "ablation: G_bi / G_pj / RoarGraph")
+                         "ablation: G_bi / G_pj / RoarGraph, update: insertion and tombstones")
     ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
