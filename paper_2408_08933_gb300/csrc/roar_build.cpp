@@ -1,29 +1,30 @@
 // RoarGraph index construction (Alg. 1-3, Sec. 4.2) for large inputs.
 //
 // The dense step (each training query's N_q nearest base rows) runs on the
-// GPU through roar_knn; connectivity enhancement's per-node beam searches run
-// on the GPU through roar_search over the projected graph. The pruning steps
-// run here on host threads, in a batched form that is deterministic for any
-// thread count:
+// GPU through roar_knn. The rest runs in a batched form that is deterministic
+// for any thread count:
 //   projection:  every pivot's list N'(x) = AcquireNeighbors(x, C(x), M, fill)
-//                is computed independently (Alg. 2, pivot selection); then every node
-//                p receives the reverse edges p -> x of all pivots x with
-//                p in N'(x) at once, re-pruned with Alg. 3 (fill) when the
-//                list would exceed M (Alg. 2, reverse-edge step);
+//                is computed independently on host threads (Alg. 2, pivot
+//                selection); then every node p receives the reverse edges
+//                p -> x of all pivots x with p in N'(x) at once, re-pruned
+//                with Alg. 3 (fill) when the list would exceed M (Alg. 2,
+//                reverse-edge step);
 //   enhancement: the rows are taken in chunks of doubling size; every row's
-//                supplementary list is AcquireNeighbors over its beam-search
-//                result without fill (Alg. 1, enhancement loop), then the chunk's
-//                reverse edges are added the same batched way, and
-//                the next chunk searches G_pj merged with all supplementary
-//                edges so far (Alg. 1's final union, formed early): on data whose
-//                clusters G_pj leaves unconnected, the reverse edges of the
-//                first rows are what lets later searches leave the medoid's
-//                cluster;
+//                beam search runs on the GPU (roar_search) and its
+//                supplementary list is AcquireNeighbors over the result and
+//                the reverse edges it already has, without fill, on the GPU
+//                (roar_acquire; Alg. 1, enhancement loop); then the chunk's
+//                reverse edges are added the same batched way (their re-pruning
+//                on the GPU too, hubs on host threads), and the next chunk
+//                searches G_pj merged with all supplementary edges so far
+//                (Alg. 1's final union, formed early): on data whose clusters
+//                G_pj leaves unconnected, the reverse edges of the first rows
+//                are what lets later searches leave the medoid's cluster;
 //   repair:      any node the final graph cannot reach from the entry gets an
 //                edge from the nearest reachable node the search finds.
 // The sequential order of the paper's loops (each pivot seeing the reverse
 // edges of earlier pivots) is replaced by these batched rounds, which is what
-// makes the host part parallel.
+// makes the work parallel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
