@@ -99,6 +99,9 @@ extern "C" roar_status roar_insert(const float *X_dev, int64_t n_total, int32_t 
     roar_index *gi = nullptr;
     if (e == cudaSuccess) rc = roar_index_create(n_total, d, X_dev, ROAR_F32, nullptr, nullptr, adj_dev, R, entry,
                                                  16384u, &gi);
+    // One query at a time: its latency is the cost, so search with a team of
+    // 8 warps per query (same results as one warp, shorter hops).
+    if (e == cudaSuccess && rc == ROAR_OK) rc = roar_index_set_tuning(gi, L, 8, 0, 0);
     std::vector<uint32_t> hid((size_t)L), hc((size_t)(M + 1) * CS), hout((size_t)(M + 1) * R), hx((size_t)M + 1);
     std::vector<int32_t> hnc((size_t)M + 1), hcnt((size_t)M + 1);
     for (int64_t v = n_old; e == cudaSuccess && rc == ROAR_OK && v < n_total; ++v) {
