@@ -87,3 +87,20 @@ def test_tiny_search_reaches_exact_result_at_full_L(tiny):
         order = np.lexsort((np.arange(len(X)), dd))[:10]
         assert ids[i].tolist() == order.tolist()
     assert np.all(visits == X.shape[0])
+
+
+def test_projection_hand_traced_on_a_circle():
+    """G_pj of the oracle's construction against a hand-traced case (Alg. 1-3)."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "projection_circle.json")) as f:
+        g = json.load(f)
+    r = np.deg2rad(np.asarray(g["angles"], np.float64))
+    X = np.zeros((len(r), 4), np.float32)
+    X[:, 0], X[:, 1] = np.cos(r), np.sin(r)
+    knn = np.asarray(g["knn"], dtype=np.uint32)
+    adj, pj, stats = oracle.build_index(X, knn, g["M"], 10, 0)
+    for v, row in g["pj"]:
+        got = [int(u) for u in pj[v] if u != 0xFFFFFFFF]
+        assert got == row, (v, got, row)
