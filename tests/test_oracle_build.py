@@ -104,3 +104,22 @@ def test_projection_hand_traced_on_a_circle():
     for v, row in g["pj"]:
         got = [int(u) for u in pj[v] if u != 0xFFFFFFFF]
         assert got == row, (v, got, row)
+
+
+def test_construction_hand_traced_on_a_circle():
+    """The oracle's whole construction (projection, connectivity enhancement,
+    final union, repair) against a hand-traced case (Alg. 1-3)."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "construction_circle.json")) as f:
+        g = json.load(f)
+    r = np.deg2rad(np.asarray(g["angles"], np.float64))
+    X = np.zeros((len(r), 4), np.float32)
+    X[:, 0], X[:, 1] = np.cos(r), np.sin(r)
+    knn = np.asarray(g["knn"], dtype=np.uint32)
+    adj, pj, stats = oracle.build_index(X, knn, g["M"], g["L"], g["entry"])
+    for v, row in g["pj"]:
+        assert [int(u) for u in pj[v] if u != 0xFFFFFFFF] == row, ("pj", v)
+    for v, row in g["adj"]:
+        assert [int(u) for u in adj[v] if u != 0xFFFFFFFF] == row, ("adj", v, adj[v].tolist())
