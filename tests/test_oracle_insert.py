@@ -1,6 +1,6 @@
-"""Invariants of insertion through the saved bipartite graph (Sec. 5.7) in
-the oracle. Parity unpinned: the steps have no closed form or printed example
-to compare with, so the checks are structural and quality properties."""
+"""Insertion through the saved bipartite graph (Sec. 5.7) in the oracle: a
+hand-traced case (two insertions, one re-pruning a full row) plus structural
+and quality properties on a larger input."""
 import numpy as np
 import pytest
 
@@ -76,3 +76,36 @@ def test_inserted_rows_are_found_and_recall_holds(inserted):
     reb, _, _ = oracle.build_index(X, knn_all, inserted["M"], inserted["L"], oracle.medoid(X))
     got_r, *_ = oracle.beam_search(X, reb, oracle.medoid(X), Q, 10, 64)
     assert oracle.recall_at_k(got, gt, 10) >= oracle.recall_at_k(got_r, gt, 10) - 0.1
+
+
+def test_insertion_hand_traced_on_a_circle():
+    """Two insertions into the hand-traced circle graph (Sec. 5.7)."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "insertion_circle.json")) as f:
+        g = json.load(f)
+
+    def unit(angles):
+        r = np.deg2rad(np.asarray(angles, np.float64))
+        V = np.zeros((len(r), 4), np.float32)
+        V[:, 0], V[:, 1] = np.cos(r), np.sin(r)
+        return V
+
+    X, T = unit(g["angles"]), unit(g["query_angles"])
+    knn = np.asarray(g["knn"], dtype=np.uint32)
+    M = g["M"]
+    R = 2 * M
+    adj = np.full((X.shape[0], R), NONE, dtype=np.uint32)
+    for v, row in enumerate(g["graph"]):
+        adj[v, :len(row)] = row
+    cap = 8
+    nout = np.full((T.shape[0], cap), NONE, dtype=np.uint32)
+    nout[:, :knn.shape[1] - 1] = knn[:, 1:]
+    cnt = np.full(T.shape[0], knn.shape[1] - 1, dtype=np.int32)
+    n_old = len(g["graph"])
+    a, no, c, q = oracle.insert(X, adj, g["entry"], n_old, T, knn[:, 0], nout, cnt, M, g["L"])
+    for v, row in enumerate(g["adj"]):
+        assert [int(u) for u in a[v] if u != NONE] == row, (v, a[v].tolist())
+    assert q.tolist() == g["chosen_q"]
+    assert no[1, :c[1]].tolist() == g["nout_t1"]
