@@ -13,9 +13,15 @@ Parity status of each function:
 * ``medoid`` -- pinned (closed form).
 * ``f32_to_bf16`` / ``f32_to_e4m3`` / decoders -- pinned (library casts).
 * ``acquire_neighbors`` (Alg. 3) -- pinned (hand case, property verifier).
-* ``beam_search`` (Sec. 4.3) -- pinned (hand-traced graphs, exact special cases).
-* ``build`` (Alg. 1-2, connectivity enhancement) -- parity unpinned: checked
-  only by invariants, as no reference graph exists to compare against.
+* ``beam_search`` (Sec. 4.3), FP32 -- pinned (hand-traced graphs, exact
+  special cases); BF16 / FP8 traversal with the FP32 re-rank of the whole
+  pool -- pinned (hand-traced case ``quant_search_fan.json``).
+* ``build_index`` (Alg. 1-2, connectivity enhancement) -- pinned (hand-traced
+  cases ``projection_circle.json``, ``construction_circle.json``) and by
+  invariants.
+* ``repair`` (reachability repair, an addition) -- pinned (hand-traced case
+  ``repair_circle.json``).
+* ``insert`` (Sec. 5.7) -- pinned (hand-traced case ``insertion_circle.json``).
 """
 from __future__ import annotations
 
@@ -88,8 +94,10 @@ def _load():
         lib.orc_acquire_neighbors.restype = i32
         lib.orc_acquire_neighbors_f32.argtypes = [P, i64, i32, u32, P, i32, i32, i32, P]
         lib.orc_acquire_neighbors_f32.restype = i32
-        lib.orc_insert.argtypes = [P, i64, i32, P, i32, u32, i64, P, i64, P, P, P, i32, i32, i32, P]
+        lib.orc_insert.argtypes = [P, i64, i32, P, i32, u32, i64, P, i64, P, P, P, i32, i32, i32, u32, P]
         lib.orc_insert.restype = i32
+        lib.orc_repair.argtypes = [P, i64, i32, P, i32, u32, P]
+        lib.orc_repair.restype = i64
         lib.orc_build.argtypes = [P, i64, i64, i32, P, i32, i32, i32, u32, P, P, P]
         lib.orc_build.restype = ctypes.c_int
         _lib = lib
@@ -196,11 +204,12 @@ def acquire_neighbors_f32(X, x: int, cand, M: int, fill: bool):
     return res[:r].copy()
 
 
-def insert(X, adj, entry: int, n_old: int, T, pivot, nout, nout_cnt, M: int, L: int):
+def insert(X, adj, entry: int, n_old: int, T, pivot, nout, nout_cnt, M: int, L: int, *, max_visits: int):
     """Insertion through the saved bipartite graph (Sec. 5.7) of rows n_old..n-1
     of X into the graph adj [n][R] (rows >= n_old empty). pivot [nt]: each
     training query's nearest base row; nout [nt][cap] / nout_cnt [nt]: N_out
-    lists. Returns (adj, nout, nout_cnt, chosen_q) updated copies."""
+    lists; max_visits: the visit cap of each new row's search. Returns (adj,
+    nout, nout_cnt, chosen_q) updated copies."""
     X = _f32(X)
     T = _f32(T)
     adj = np.ascontiguousarray(adj, dtype=np.uint32).copy()
@@ -210,10 +219,24 @@ def insert(X, adj, entry: int, n_old: int, T, pivot, nout, nout_cnt, M: int, L: 
     n, d = X.shape
     chosen = np.full(n - n_old, -1, dtype=np.int32)
     rc = _load().orc_insert(_p(X), n, d, _p(adj), adj.shape[1], entry, n_old, _p(T), T.shape[0], _p(pivot),
-                            _p(nout), _p(nout_cnt), nout.shape[1], M, L, _p(chosen))
+                            _p(nout), _p(nout_cnt), nout.shape[1], M, L, max_visits, _p(chosen))
     if rc != 0:
         raise ValueError(f"orc_insert failed: {rc}")
     return adj, nout, nout_cnt, chosen
+
+
+def repair(X, adj, entry: int):
+    """Reachability repair (an addition to Alg. 1; see roar_oracle.c) of a
+    graph adj [n][R] with compact rows. Returns (repaired copy, repairs,
+    nodes unreachable before the first repair)."""
+    X = _f32(X)
+    adj = np.ascontiguousarray(adj, dtype=np.uint32).copy()
+    n, d = X.shape
+    u0 = np.zeros(1, dtype=np.int64)
+    r = _load().orc_repair(_p(X), n, d, _p(adj), adj.shape[1], entry, _p(u0))
+    if r < 0:
+        raise MemoryError("orc_repair")
+    return adj, int(r), int(u0[0])
 
 
 def build_index(X, knn_ids, M: int, L: int, entry: int):

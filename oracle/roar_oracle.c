@@ -36,9 +36,13 @@
  *     reachability): every node not reachable from the entry gets an edge
  *     from its nearest reachable node.
  *
- * Parity status: the search, the distance, the quantisers and Alg. 3 are
- * pinned by tests; the construction is pinned only by invariants (no code or
- * data from the authors exists to compare graphs against).
+ * Parity status (each pin is a test under tests/, with hand-derived golden
+ * cases under tests/golden/): the distance, the quantisers, the FP32 search,
+ * the quantised search with its FP32 re-rank, Alg. 3, the projection and
+ * connectivity enhancement of Alg. 1-2, the reachability repair, deletion
+ * and insertion are each pinned by a hand-traced case as well as by
+ * invariants; no code or data from the authors exists to compare whole
+ * graphs against.
  */
 #include <math.h>
 #include <stdint.h>
@@ -642,25 +646,71 @@ static int32_t beam_search_f64_lists(const float *X, int64_t n, int32_t d, const
     return size;
 }
 
-static int64_t bfs_mark(const ulist *G, int64_t n, uint32_t src, unsigned char *reach, uint32_t *queue) {
-    int64_t head = 0, tail = 0, cnt = 0;
-    if (reach[src]) return 0;
-    reach[src] = 1;
-    queue[tail++] = src;
-    ++cnt;
-    while (head < tail) {
-        uint32_t v = queue[head++];
-        for (int32_t j = 0; j < G[v].n; ++j) {
-            uint32_t u = G[v].v[j];
-            if (!reach[u]) {
-                reach[u] = 1;
-                queue[tail++] = u;
-                ++cnt;
+/*
+ * Reachability repair (an addition: the paper states that connectivity
+ * enhancement makes every base node reachable, Sec. 4.2.3, but its
+ * algorithm does not guarantee it). adj [n][R]: rows of ids, each compact
+ * (edges first, then 0xFFFFFFFF padding), modified in place. While some node
+ * is not reachable from the entry:
+ *   u = the smallest unreachable id;
+ *   among the reachable nodes with a free slot, r = the nearest to u
+ *     (FP64 delta(u, r) = -<x_u, x_r>, ties to the lower id): u is appended
+ *     to r's row;
+ *   when every reachable node is full, r = the nearest of them (same order)
+ *     gives up its last edge, which becomes r -> u;
+ *   reachability is recomputed (breadth-first from the entry).
+ * Returns the number of repairs (-1 when out of memory); *unreachable0 gets
+ * the number of nodes unreachable before the first repair.
+ */
+int64_t orc_repair(const float *X, int64_t n, int32_t d, uint32_t *adj, int32_t R, uint32_t entry,
+                   int64_t *unreachable0) {
+    unsigned char *reach = (unsigned char *)malloc((size_t)n);
+    uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!reach || !queue) { free(reach); free(queue); return -1; }
+    int64_t repairs = 0;
+    for (;;) {
+        /* breadth-first marking from the entry */
+        memset(reach, 0, (size_t)n);
+        int64_t head = 0, tail = 0;
+        reach[entry] = 1;
+        queue[tail++] = entry;
+        while (head < tail) {
+            const uint32_t v = queue[head++];
+            for (int32_t j = 0; j < R; ++j) {
+                const uint32_t w = adj[(int64_t)v * R + j];
+                if (w == ORC_NONE || (int64_t)w >= n || reach[w]) continue;
+                reach[w] = 1;
+                queue[tail++] = w;
             }
         }
+        if (repairs == 0 && unreachable0) *unreachable0 = n - tail;
+        if (tail == n) break;
+        uint32_t u = 0;
+        while (reach[u]) ++u;
+        int64_t best = -1, bestfull = -1;
+        double bd = INFINITY, bdf = INFINITY;
+        for (int64_t r = 0; r < n; ++r) {
+            if (!reach[r]) continue;
+            const double dd = dist64(X + (int64_t)u * d, X + r * d, d);
+            if (adj[r * R + R - 1] == ORC_NONE) {
+                if (dd < bd) { bd = dd; best = r; }
+            } else if (dd < bdf) {
+                bdf = dd;
+                bestfull = r;
+            }
+        }
+        if (best >= 0) {
+            int32_t j = 0;
+            while (adj[best * R + j] != ORC_NONE) ++j;
+            adj[best * R + j] = u;
+        } else {
+            adj[bestfull * R + R - 1] = u;
+        }
+        ++repairs;
     }
-    (void)n;
-    return cnt;
+    free(reach);
+    free(queue);
+    return repairs;
 }
 
 /*
@@ -694,10 +744,7 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
     unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
     unsigned char *visited = (unsigned char *)malloc((size_t)n);
     unsigned char *checked = (unsigned char *)malloc((size_t)L);
-    unsigned char *reach = (unsigned char *)malloc((size_t)n);
-    uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
-    if (!B || !Gpj || !Gp || !F || !buf || !res || !snap || !seen || !visited || !checked ||
-        !reach || !queue)
+    if (!B || !Gpj || !Gp || !F || !buf || !res || !snap || !seen || !visited || !checked)
         goto done;
     for (int64_t t = 0; t < nt; ++t)
         for (int32_t r = 0; r < nqd; ++r)
@@ -783,48 +830,22 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
                 if (ul_push(&F[v], Gp[v].v[j])) goto done;
     }
 
-    /* Reachability repair: each unreachable u (ascending) gets an edge from
-     * its nearest reachable node r (FP64, ties to the lower id), preferring
-     * nodes with a free slot; a full r gives up its last edge. */
+    /* Final adjacency rows (compact, then padding), before the repair. */
     const int32_t R = 2 * M;
-    memset(reach, 0, (size_t)n);
-    int64_t nreach = bfs_mark(F, n, entry, reach, queue);
-    int64_t unreachable0 = n - nreach;
-    while (nreach < n) {
-        uint32_t u = 0;
-        while (reach[u]) ++u;
-        int64_t best = -1, bestfull = -1;
-        double bd = INFINITY, bdf = INFINITY;
-        for (int64_t r = 0; r < n; ++r) {
-            if (!reach[r]) continue;
-            double dd = dist64(X + (int64_t)u * d, X + r * d, d);
-            if (F[r].n < R) {
-                if (dd < bd) { bd = dd; best = r; }
-            } else if (dd < bdf) {
-                bdf = dd;
-                bestfull = r;
-            }
-        }
-        if (best >= 0) {
-            if (ul_push(&F[best], u)) goto done;
-        } else {
-            F[bestfull].v[F[bestfull].n - 1] = u;
-        }
-        ++repairs;
-        memset(reach, 0, (size_t)n);
-        nreach = bfs_mark(F, n, entry, reach, queue);
-    }
-
-    int64_t pj_edges = 0, fin_edges = 0;
+    int64_t pj_edges = 0;
     for (int64_t v = 0; v < n; ++v) {
         pj_edges += Gpj[v].n;
-        fin_edges += F[v].n;
         if (pj_out)
             for (int32_t j = 0; j < M; ++j)
                 pj_out[v * M + j] = j < Gpj[v].n ? Gpj[v].v[j] : ORC_NONE;
         for (int32_t j = 0; j < R; ++j)
             adj_out[v * R + j] = j < F[v].n ? F[v].v[j] : ORC_NONE;
     }
+    int64_t unreachable0 = 0;
+    repairs = orc_repair(X, n, d, adj_out, R, entry, &unreachable0);
+    if (repairs < 0) goto done;
+    int64_t fin_edges = 0;
+    for (int64_t v = 0; v < n * R; ++v) fin_edges += adj_out[v] != ORC_NONE;
     if (stats) {
         stats[0] = pivots;
         stats[1] = proj_reprunes;
@@ -847,8 +868,6 @@ done:
     free(seen);
     free(visited);
     free(checked);
-    free(reach);
-    free(queue);
     return rc;
 }
 
@@ -858,8 +877,8 @@ done:
  * time in id order (rows n_old .. n_total-1 of X; their adjacency rows start
  * empty and nothing links to them, so searches cannot reach them before
  * their turn). For new row v:
- *   1. beam search (FP32, width L, visit cap 16384) of X[v] from the entry
- *      over the current graph;
+ *   1. beam search (FP32, width L, visit cap max_visits) of X[v] from the
+ *      entry over the current graph;
  *   2. the first pool entry b that some training query is connected to (b is
  *      in N_out(t), or b is the nearest base row (pivot) of t);
  *   3. of those queries, q = the one nearest to v (-dot_fixed, ties by id);
@@ -892,9 +911,10 @@ static void sort_by_fixed_dist(const float *X, int32_t d, const float *xv, uint3
 
 int orc_insert(const float *X, int64_t n_total, int32_t d, uint32_t *adj, int32_t R, uint32_t entry,
                int64_t n_old, const float *T, int64_t nt, const uint32_t *pivot, uint32_t *nout,
-               int32_t *nout_cnt, int32_t nout_cap, int32_t M, int32_t L, int32_t *chosen_q) {
+               int32_t *nout_cnt, int32_t nout_cap, int32_t M, int32_t L, uint32_t max_visits,
+               int32_t *chosen_q) {
     if (n_old < 1 || n_total < n_old || (int64_t)entry >= n_old || d < 1 || R < 1 || M < 1 || M > R ||
-        L < 1 || nt < 1 || nout_cap < 1)
+        L < 1 || nt < 1 || nout_cap < 1 || max_visits < 1)
         return ORC_EINVAL;
     /* queries connected to each base row: in-edges from N_out, and pivot edges */
     ulist *inc = (ulist *)calloc((size_t)n_total, sizeof(ulist));
@@ -919,7 +939,7 @@ int orc_insert(const float *X, int64_t n_total, int32_t d, uint32_t *adj, int32_
         const float *xv = X + v * d;
         int32_t size = 0;
         uint32_t nv = 0, nh = 0;
-        search_one(0, X, NULL, n_total, d, adj, R, entry, xv, L, 16384u, pool, &size, &nv, &nh, NULL, 0,
+        search_one(0, X, NULL, n_total, d, adj, R, entry, xv, L, max_visits, pool, &size, &nv, &nh, NULL, 0,
                    visited, tmp);
         int64_t q = -1;
         for (int32_t r = 0; r < size && q < 0; ++r) {

@@ -30,7 +30,7 @@ def test_insert_matches_oracle(n, n_old, M, L):
     nout = np.full((T.shape[0], cap), NONE, dtype=np.uint32)
     nout[:, :nq - 1] = knn[:, 1:]
     cnt = np.full(T.shape[0], nq - 1, dtype=np.int32)
-    r_adj, r_nout, r_cnt, r_q = oracle.insert(X, adj, entry, n_old, T, knn[:, 0], nout, cnt, M, L)
+    r_adj, r_nout, r_cnt, r_q = oracle.insert(X, adj, entry, n_old, T, knn[:, 0], nout, cnt, M, L, max_visits=16384)
 
     dev = torch.device("cuda:0")
     Xd = torch.from_numpy(X).to(dev)

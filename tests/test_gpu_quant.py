@@ -72,3 +72,29 @@ def test_quantized_recall_close_to_fp32(tiny):
         got = run(idx, Q, 10, 100)
         idx.close()
         assert abs(oracle.recall_at_k(got[0], gt, 10) - r32) <= 0.005, dtype
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+def test_hand_traced_quantized_case(dtype):
+    """The hand-traced case of tests/golden/quant_search_fan.json on the GPU:
+    the FP8 scale multiplies once after the fixed-order dot (a tie that one
+    rounding decides), the whole final pool is re-ranked in FP32 and ties go
+    to the lower id."""
+    from conftest import load_golden
+    from test_oracle_search import quant_fan_inputs
+
+    g = load_golden("quant_search_fan.json")
+    X32, adj, q, fp8, scales, bf16 = quant_fan_inputs(g)
+    if dtype == "f32":
+        idx = dev_index(X32, adj, g["entry"], max_visits=MV)
+    elif dtype == "bf16":
+        idx = dev_index(X32, adj, g["entry"], dtype="bf16", trav=bf16.view(np.int16), max_visits=MV)
+    else:
+        idx = dev_index(X32, adj, g["entry"], dtype="fp8", trav=fp8, scales=scales, max_visits=MV)
+    e = g["expect"][dtype]
+    for k in (1, 2):
+        ids, dist, visits, hops, st = run(idx, q, k, g["L"])
+        assert ids[0].tolist() == e[str(k)]["ids"], k
+        assert dist[0].tolist() == e[str(k)]["dist"], k
+        assert (int(visits[0]), int(hops[0]), int(st[0])) == (e["visits"], e["hops"], 0)
+    idx.close()

@@ -1,13 +1,16 @@
-"""Invariants of the oracle's index construction (Alg. 1-3, Sec. 4.2).
+"""Pins of the oracle's index construction (Alg. 1-3, Sec. 4.2).
 
-Parity of the construction itself is unpinned (no reference graph exists);
-these tests check what the paper states the graph must satisfy.
+Hand-traced cases fix the projection, connectivity enhancement and the
+reachability repair step by step; invariants check what the paper states
+the graph must satisfy. (No graph from the authors exists to compare a
+whole index against.)
 """
 from collections import deque
 
 import numpy as np
 
 import oracle
+from conftest import load_golden
 
 NONE = 0xFFFFFFFF
 
@@ -123,3 +126,19 @@ def test_construction_hand_traced_on_a_circle():
         assert [int(u) for u in pj[v] if u != 0xFFFFFFFF] == row, ("pj", v)
     for v, row in g["adj"]:
         assert [int(u) for u in adj[v] if u != 0xFFFFFFFF] == row, ("adj", v, adj[v].tolist())
+
+
+def test_hand_traced_reachability_repair():
+    """The repair step (an addition to Alg. 1) on a hand-traced case with all
+    three of its branches: nearest reachable node with room, nearest full but
+    another with room, every reachable node full (the last edge is evicted)."""
+    g = load_golden("repair_circle.json")
+    a = np.deg2rad(np.array(g["angles_deg"], np.float64))
+    X = np.zeros((len(a), 4), np.float32)
+    X[:, 0], X[:, 1] = np.cos(a), np.sin(a)
+    adj, repairs, unreach = oracle.repair(X, np.array(g["adj"], np.uint32), g["entry"])
+    assert adj.tolist() == g["expect_adj"]
+    assert (repairs, unreach) == (g["expect_repairs"], g["expect_unreachable_before"])
+    # already connected: nothing to do
+    adj2, r2, u2 = oracle.repair(X, adj, g["entry"])
+    assert adj2.tolist() == adj.tolist() and (r2, u2) == (0, 0)

@@ -26,7 +26,7 @@ def inserted():
     nout = np.full((T.shape[0], cap), NONE, dtype=np.uint32)
     nout[:, :nq - 1] = knn[:, 1:]
     cnt = np.full(T.shape[0], nq - 1, dtype=np.int32)
-    out = oracle.insert(X, adj, entry, n_old, T, knn[:, 0], nout, cnt, M, L)
+    out = oracle.insert(X, adj, entry, n_old, T, knn[:, 0], nout, cnt, M, L, max_visits=16384)
     return dict(X=X, T=T, w=w, n_old=n_old, M=M, L=L, R=R, entry=entry, knn=knn, before=(adj, nout, cnt),
                 after=out)
 
@@ -104,7 +104,7 @@ def test_insertion_hand_traced_on_a_circle():
     nout[:, :knn.shape[1] - 1] = knn[:, 1:]
     cnt = np.full(T.shape[0], knn.shape[1] - 1, dtype=np.int32)
     n_old = len(g["graph"])
-    a, no, c, q = oracle.insert(X, adj, g["entry"], n_old, T, knn[:, 0], nout, cnt, M, g["L"])
+    a, no, c, q = oracle.insert(X, adj, g["entry"], n_old, T, knn[:, 0], nout, cnt, M, g["L"], max_visits=16384)  # does not bind: each traced search visits at most n rows
     for v, row in enumerate(g["adj"]):
         assert [int(u) for u in a[v] if u != NONE] == row, (v, a[v].tolist())
     assert q.tolist() == g["chosen_q"]

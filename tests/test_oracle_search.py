@@ -113,3 +113,32 @@ def test_tombstones_filter_the_same_traversal(tiny):
     for i in range(Q.shape[0]):
         alive = [u for u in full[0][i].tolist() if u != 0xFFFFFFFF and not deleted[u]][:10]
         assert got[0][i].tolist() == alive + [0xFFFFFFFF] * (10 - len(alive))
+
+
+def quant_fan_inputs(g):
+    """Arrays of the hand-traced quantised-search case (tests/golden/quant_search_fan.json)."""
+    X32 = np.array(g["x32"], np.float32)
+    adj = np.array(g["adj"], np.uint32)
+    q = np.array([g["q"]], np.float32)
+    fp8 = np.array(g["fp8_codes"], np.uint8)
+    scales = np.array(g["fp8_scale_bits"], np.uint32).view(np.float32)
+    bf16 = np.array(g["bf16_codes"], np.uint16)
+    return X32, adj, q, fp8, scales, bf16
+
+
+def test_hand_traced_quantized_search_and_rerank():
+    """BF16 / FP8 traversal with one FP32 scale multiply after the fixed-order
+    dot, the FP32 re-rank of the whole final pool, ties by id (hand-traced)."""
+    g = load_golden("quant_search_fan.json")
+    X32, adj, q, fp8, scales, bf16 = quant_fan_inputs(g)
+    assert [oracle.e4m3_to_f32(int(c)) for c in fp8[1]] == [0.125, 0.625, 0.0, 0.0]
+    assert scales[1] == np.float32(1 + 2.0 ** -23)
+    forms = {"fp8": dict(dtype="fp8", Xt=fp8, scales=scales), "bf16": dict(dtype="bf16", Xt=bf16),
+             "f32": dict(dtype="f32")}
+    for name, kw in forms.items():
+        e = g["expect"][name]
+        for k in (1, 2):
+            ids, dist, visits, hops, st = oracle.beam_search(X32, adj, g["entry"], q, k, g["L"], **kw)
+            assert ids[0].tolist() == e[str(k)]["ids"], (name, k)
+            assert dist[0].tolist() == e[str(k)]["dist"], (name, k)
+            assert (int(visits[0]), int(hops[0]), int(st[0])) == (e["visits"], e["hops"], 0), name
