@@ -237,8 +237,9 @@ roar_status roar_autotune(roar_index *idx, const float *queries, int64_t nq, int
  * and, per resident warp, a visited bitmap of ceil(n/32) words and a visit
  * log of max_visits + ROAR_MAX_RMAX ids; the number of warps used is what fits
  * (fewer than roar_search on large n, so it can be slower). Sizes that do not
- * fit even 4 warps (4 * 4 * (ceil(n/32) + max_visits + 128) bytes > 64 MiB,
- * e.g. n above about 120 million at the default max_visits) return
+ * fit even 4 warps (4 * 4 * (ceil(n/32) + max_visits + 128) bytes above
+ * 64 MiB - 512 bytes, e.g. n above about 133 million at the default
+ * max_visits of 16384) return
  * ROAR_EINVAL with an explanation in roar_last_error().
  * The first call on each device, with that device current, looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
@@ -329,6 +330,18 @@ roar_status roar_quantize(const float *X, int64_t n, int32_t d, roar_dtype dtype
  */
 roar_status roar_knn(const float *T, int64_t nt, const float *X, int64_t n, int32_t d, int32_t kk,
                      uint32_t *ids, float *dist, void *stream);
+
+/*
+ * Testing hook of roar_knn's failure handling (no counterpart in the paper):
+ * sets, for the whole process, the wall-time limit of each bounded wait
+ * (mbarrier phase) inside the tensor-core kernel. ns < 0 restores the default
+ * of 2 s. ns == 0 makes every wait give up as soon as its phase is found
+ * incomplete, so a following roar_knn returns ROAR_ETIMEOUT through the same
+ * path a real stall would take (the kernel waits for its copies and issued
+ * MMAs, frees its TMEM and returns) without faulting anything. Affects
+ * launches made after the call. Always returns ROAR_OK.
+ */
+roar_status roar_knn_set_wait_limit_ns(int64_t ns);
 
 /*
  * Medoid entry point (Sec. 4.2.4, Sec. 4.3), read as the base row nearest in

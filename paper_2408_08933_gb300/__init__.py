@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.roar_quantize.restype = ctypes.c_int
     L.roar_knn.argtypes = [P, i64, P, i64, i32, i32, P, P, P]
     L.roar_knn.restype = ctypes.c_int
+    L.roar_knn_set_wait_limit_ns.argtypes = [i64]
+    L.roar_knn_set_wait_limit_ns.restype = ctypes.c_int
     L.roar_medoid.argtypes = [P, i64, i32, i32, ctypes.POINTER(u32)]
     L.roar_medoid.restype = ctypes.c_int
     L.roar_acquire.argtypes = [P, i64, i32, P, i64, P, i32, P, i32, i32, P, P, P, P]
@@ -229,6 +231,12 @@ def roar_quantize(X, n, d, dtype, out, scales, stream=None):
 
 def roar_knn(T, nt, X, n, d, kk, ids, dist, stream=None):
     _check(lib().roar_knn(T, nt, X, n, d, kk, ids, dist, stream), "roar_knn")
+
+
+def roar_knn_set_wait_limit_ns(ns):
+    """Testing hook: wall-time limit of each bounded wait in roar_knn's kernel
+    (ns < 0: the 2 s default; 0: give up at the first incomplete phase)."""
+    _check(lib().roar_knn_set_wait_limit_ns(int(ns)), "roar_knn_set_wait_limit_ns")
 
 
 def roar_acquire(X, n, d, xs, nx, cand, cand_stride, ncand, M, fill, out, out_cnt, sorted_out=None,

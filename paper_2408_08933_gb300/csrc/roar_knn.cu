@@ -17,6 +17,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "roar_internal.cuh"
@@ -149,8 +150,17 @@ namespace roar {
 size_t knn_tc_smem_bytes(int d);
 cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloat16 *X16, int64_t n, int d,
                           int C, int cap, float *buf_s, uint32_t *buf_i, uint32_t *cand, int *err,
-                          cudaStream_t s);
+                          uint64_t wait_ns, cudaStream_t s);
+// Wall-time limit of each bounded wait in the tensor-core kernel: 2 s by
+// default, far above any legitimate wait there.
+constexpr int64_t kKnnWaitDefaultNs = 2000000000ll;
+static std::atomic<int64_t> g_knn_wait_ns{kKnnWaitDefaultNs};
 }  // namespace roar
+
+extern "C" roar_status roar_knn_set_wait_limit_ns(int64_t ns) {
+    g_knn_wait_ns.store(ns < 0 ? kKnnWaitDefaultNs : ns);
+    return ROAR_OK;
+}
 
 extern "C" roar_status roar_knn(const float *T, int64_t nt, const float *X, int64_t n, int32_t d,
                                 int32_t kk, uint32_t *ids, float *dist, void *stream) {
@@ -168,6 +178,7 @@ extern "C" roar_status roar_knn(const float *T, int64_t nt, const float *X, int6
     float *bs = nullptr;
     uint32_t *bi = nullptr, *cand = nullptr;
     int *err = nullptr;
+    const uint64_t wait_ns = (uint64_t)g_knn_wait_ns.load();
     roar_status rc = ROAR_OK;
     int herr = 0;
     cudaError_t e = cudaMalloc(&t16, (size_t)nt * d * 2);
@@ -187,7 +198,7 @@ extern "C" roar_status roar_knn(const float *T, int64_t nt, const float *X, int6
     if ((rc = quantize_bf16(X, n, d, x16, s)) != ROAR_OK) goto done;
     for (int64_t r0 = 0; r0 < nt; r0 += RB) {
         const int64_t rb = std::min(RB, nt - r0);
-        e = knn_tc_launch(t16 + r0 * d, rb, x16, n, d, C, CAP, bs, bi, cand, err, s);
+        e = knn_tc_launch(t16 + r0 * d, rb, x16, n, d, C, CAP, bs, bi, cand, err, wait_ns, s);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "roar_knn: tensor-core scores");
             goto done;

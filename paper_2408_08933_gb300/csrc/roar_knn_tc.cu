@@ -18,8 +18,9 @@
 // threshold. At the end each row's best C candidates are written out
 // (unsorted) for the exact FP32 re-score.
 //
-// Every mbarrier wait is bounded: on timeout the kernel sets *err, waits for
-// its own copies, frees its TMEM and returns.
+// Every mbarrier wait is bounded (wait_ns of wall time per wait): on timeout
+// the kernel sets *err, waits for its own copies and for the MMAs it has
+// issued, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "roar_internal.cuh"
@@ -38,7 +39,7 @@ constexpr int kMmaWarp = 2;        // lane 0 issues the MMAs; the warp owns TMEM
 constexpr int kThreads = 7 * 32;
 constexpr int kMaxStages = 4;
 constexpr int kCap = 1024;         // candidate buffer entries per row
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: far above any legitimate wait here
+constexpr uint64_t kDrainNs = 2000000000ull;  // bound of the final wait for issued MMAs
 constexpr int kTmemCols = 512;     // two 256-column accumulators
 constexpr uint32_t kChunkA = kTM * kKC * 2;   // 16 KB
 constexpr uint32_t kChunkB = kTN * kKC * 2;   // 32 KB
@@ -71,28 +72,63 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase with the given parity: gives up (and raises the
-// CTA's abort flag) after kWaitNs of wall time, or as soon as another role
-// aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// CTA's abort flag) after wait_ns of wall time, or as soon as another role
+// aborted. wait_ns == 0 gives up as soon as the phase is found incomplete
+// (a test setting: it makes the timeout path run without any fault).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, uint64_t wait_ns) {
+    if (wait_ns == 0) {
+        if (mbar_test(bar, parity)) return true;
+        *abort = 1;
+        return false;
+    }
     uint64_t deadline = 0;
     for (uint32_t i = 0;; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_try(bar, parity)) return true;
         if (*abort) return false;
         if ((i & 63) == 0) {
             const uint64_t now = global_ns();
-            if (deadline == 0) deadline = now + kWaitNs;
+            if (deadline == 0) deadline = now + wait_ns;
             else if (now > deadline) {
                 *abort = 1;
                 return false;
             }
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag: the final wait for the MMAs this
+// thread issued (they always complete; the bound only keeps the wait finite).
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity) {
+    uint64_t deadline = 0;
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            const uint64_t now = global_ns();
+            if (deadline == 0) deadline = now + kDrainNs;
+            else if (now > deadline) return false;
         }
     }
 }
@@ -251,9 +287,10 @@ __device__ __forceinline__ void stage_chunk(uint32_t dst, const __nv_bfloat16 *s
 __global__ void __launch_bounds__(kThreads, 1)
 knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat16 *__restrict__ X,
               int64_t n, int d, int stages, int C, float *__restrict__ buf_s,
-              uint32_t *__restrict__ buf_i, uint32_t *__restrict__ out_i, int *__restrict__ err) {
+              uint32_t *__restrict__ buf_i, uint32_t *__restrict__ out_i, int *__restrict__ err,
+              uint64_t wait_ns) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], acc_full[2], acc_empty[2], a_full;
+    __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], acc_full[2], acc_empty[2], a_full, drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     volatile int *abort_v = &abort_flag;
@@ -276,6 +313,7 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
             mbar_init(&acc_empty[b], 4 * 32);
         }
         mbar_init(&a_full, kProducers);
+        mbar_init(&drain_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -296,7 +334,7 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
         for (int64_t g = 0; g < nchunks; ++g) {
             const int s = (int)(g % stages);
             const uint32_t use = (uint32_t)(g / stages);
-            if (use > 0 && !mbar_wait(&empty_bar[s], (use - 1) & 1, abort_v)) break;
+            if (use > 0 && !mbar_wait(&empty_bar[s], (use - 1) & 1, abort_v, wait_ns)) break;
             const int64_t t = g / nkc;
             const int c = (int)(g - t * nkc);
             stage_chunk(b_base + (uint32_t)s * kChunkB, X, t * kTN, kTN, n, d, c * kKC, tid, kProducers);
@@ -305,34 +343,45 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
         cp_async_wait<0>();
     } else if (warp == kMmaWarp) {
         // ---- MMA issue ----
-        if (lane == 0 && mbar_wait(&a_full, 0, abort_v)) {
-            fence_async_smem();  // cp.async data, written through the generic proxy, to the tensor core
-            int64_t g = 0;
-            bool ok = true;
-            for (int64_t t = 0; t < ntiles && ok; ++t) {
-                const int b = (int)(t & 1);
-                const uint32_t ub = (uint32_t)(t >> 1);
-                if (ub > 0 && !mbar_wait(&acc_empty[b], (ub - 1) & 1, abort_v)) break;
-                tc_fence_after();
-                for (int c = 0; c < nkc; ++c, ++g) {
-                    const int s = (int)(g % stages);
-                    if (!mbar_wait(&full_bar[s], (uint32_t)(g / stages) & 1, abort_v)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_async_smem();
+        if (lane == 0) {
+            bool issued = false;
+            if (mbar_wait(&a_full, 0, abort_v, wait_ns)) {
+                fence_async_smem();  // cp.async data, written through the generic proxy, to the tensor core
+                int64_t g = 0;
+                bool ok = true;
+                for (int64_t t = 0; t < ntiles && ok; ++t) {
+                    const int b = (int)(t & 1);
+                    const uint32_t ub = (uint32_t)(t >> 1);
+                    if (ub > 0 && !mbar_wait(&acc_empty[b], (ub - 1) & 1, abort_v, wait_ns)) break;
                     tc_fence_after();
-                    const uint32_t a_chunk = a_base + (uint32_t)c * kChunkA;
-                    const uint32_t b_chunk = b_base + (uint32_t)s * kChunkB;
+                    for (int c = 0; c < nkc; ++c, ++g) {
+                        const int s = (int)(g % stages);
+                        if (!mbar_wait(&full_bar[s], (uint32_t)(g / stages) & 1, abort_v, wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_async_smem();
+                        tc_fence_after();
+                        const uint32_t a_chunk = a_base + (uint32_t)c * kChunkA;
+                        const uint32_t b_chunk = b_base + (uint32_t)s * kChunkB;
 #pragma unroll
-                    for (int ks = 0; ks < kKC / 16; ++ks) {
-                        const uint64_t ad = smem_desc(a_chunk + ks * 256, 128, 1024);
-                        const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024);
-                        tc_mma(tmem + (uint32_t)(b * kTN), ad, bd, (c > 0 || ks > 0) ? 1u : 0u);
+                        for (int ks = 0; ks < kKC / 16; ++ks) {
+                            const uint64_t ad = smem_desc(a_chunk + ks * 256, 128, 1024);
+                            const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024);
+                            tc_mma(tmem + (uint32_t)(b * kTN), ad, bd, (c > 0 || ks > 0) ? 1u : 0u);
+                        }
+                        issued = true;
+                        tc_commit(&empty_bar[s]);
                     }
-                    tc_commit(&empty_bar[s]);
+                    if (ok) tc_commit(&acc_full[b]);
                 }
-                if (ok) tc_commit(&acc_full[b]);
+            }
+            // Every MMA this thread issued has finished (it may still be
+            // writing TMEM and reading shared memory after an abort) before
+            // the CTA frees its TMEM and exits.
+            if (issued) {
+                tc_commit(&drain_bar);
+                if (!mbar_drain(&drain_bar, 0)) *abort_v = 1;
             }
         }
         __syncwarp();
@@ -352,7 +401,8 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
         bool done = true;
         for (int64_t t = 0; t < ntiles; ++t) {
             const int b = (int)(t & 1);
-            if (!mbar_wait(&acc_full[b], (uint32_t)(t >> 1) & 1, abort_v)) {
+            // The warp leaves together: the TMEM loads below are warp-collective.
+            if (!__all_sync(kFull, mbar_wait(&acc_full[b], (uint32_t)(t >> 1) & 1, abort_v, wait_ns))) {
                 done = false;
                 break;
             }
@@ -415,8 +465,7 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
                 }
             }
         }
-        if (done && !*abort_v) {
-            __syncwarp();
+        if (__all_sync(kFull, done && !*abort_v)) {
             uint32_t over = __ballot_sync(kFull, row_ok && cnt > C);
             while (over) {
                 const int src = __ffs(over) - 1;
@@ -457,7 +506,7 @@ size_t knn_tc_smem_bytes(int d) {
 // against X16 into cand [nt][C]; buf_s/buf_i are [nt][cap] scratch.
 cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloat16 *X16, int64_t n, int d,
                           int C, int cap, float *buf_s, uint32_t *buf_i, uint32_t *cand, int *err,
-                          cudaStream_t s) {
+                          uint64_t wait_ns, cudaStream_t s) {
     const int stages = knn_tc_stages(d);
     // A cut must leave room for a whole tile: C + kTN <= kCap.
     if (stages < 2 || cap != kCap || C < 1 || C + kTN > kCap) return cudaErrorInvalidValue;
@@ -466,7 +515,7 @@ cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloa
     if (e != cudaSuccess) return e;
     const int64_t blocks = (nt + kTM - 1) / kTM;
     knn_tc_kernel<<<(unsigned)blocks, kThreads, smem, s>>>(T16, nt, X16, n, d, stages, C, buf_s, buf_i,
-                                                           cand, err);
+                                                           cand, err, wait_ns);
     return cudaGetLastError();
 }
 

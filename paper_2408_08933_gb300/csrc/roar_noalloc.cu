@@ -81,10 +81,13 @@ extern "C" roar_status roar_search_noalloc(int64_t n, int32_t d, const float *ba
     const int32_t log_cap = (int32_t)max_visits + ROAR_MAX_RMAX;
     const size_t per_slot = (size_t)words * 4 + (size_t)log_cap * 4;
     const size_t head = 256;
-    const int64_t slots_fit = (int64_t)((kScratchBytes - head) / per_slot);
+    // The logs start on a 256-byte boundary after the bitmaps: keep 256 bytes
+    // for that padding, so every slot count up to slots_fit fits the array.
+    const int64_t slots_fit = (int64_t)((kScratchBytes - head - 256) / per_slot);
     if (slots_fit < kWarpsPerBlock) {
         set_error("roar_search_noalloc: n or max_visits too large for the fixed 64 MiB scratch "
-                  "(needs 4 * (ceil(n/32) + max_visits + 128) bytes per warp, 4 warps at least)");
+                  "(needs 4 * (ceil(n/32) + max_visits + 128) bytes per warp, 4 warps at least, "
+                  "within 64 MiB - 512 bytes)");
         return ROAR_EINVAL;
     }
     int dev = 0;
