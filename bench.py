@@ -125,7 +125,7 @@ def _setup(w, torch, pkg, rs, log):
                      "paper_2408_08933_gb300/csrc/roar_knn.cu", "paper_2408_08933_gb300/csrc/roar_knn_tc.cu",
                      "paper_2408_08933_gb300/csrc/roar_search_kernel.cuh",
                      "paper_2408_08933_gb300/csrc/roar_search.cu"])
-    cache = os.path.join(CACHE_DIR, f"{w.name}_{w.n}_{w.n_train}_{w.n_test}_{w.offset_norm}_{w.noise}_{key}.npz")
+    cache = os.path.join(CACHE_DIR, f"{w.name}_{w.n}_{w.n_train}_{w.n_test}_{w.n_comp}_{w.offset_norm}_{w.noise}_{key}.npz")
     t0 = time.time()
     X = rs.base(w)
     Q = rs.test_queries(w)
@@ -213,6 +213,8 @@ def _algorithmic_bytes(visits, hops, deg_mean, d, elem_bytes, scale_bytes, k_rer
 
 
 def _cpu_baseline(X, adj_np, entry, Q, L, budget_s=12.0):
+    """The oracle's beam search on the host cores over a bounded sample of the
+    test queries. Returns (baseline dict, the oracle's results for Q[:n])."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
 
@@ -221,18 +223,70 @@ def _cpu_baseline(X, adj_np, entry, Q, L, budget_s=12.0):
     oracle.beam_search(X, adj_np, entry, Q[:8], 10, L, max_visits=16384)
     per_q = max(1e-5, (time.time() - t0) / 8)
     n = int(min(len(Q), max(cores * 4, budget_s * cores / per_q)))
-    chunks = np.array_split(np.arange(n), cores * 4)
+    chunks = [c for c in np.array_split(np.arange(n), cores * 4) if len(c)]
 
     def work(ix):
         return oracle.beam_search(X, adj_np, entry, Q[ix], 10, L, max_visits=16384)
 
     t0 = time.time()
     with ThreadPoolExecutor(max_workers=cores) as ex:
-        list(ex.map(work, [c for c in chunks if len(c)]))
+        parts = list(ex.map(work, chunks))
     dt = time.time() - t0
-    return {"value": n / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} of the {len(Q)} test queries at L={L}, k=10, one query per call chunk "
-                      f"on {cores} threads"}
+    ref = tuple(np.concatenate([p[i] for p in parts]) for i in range(5))
+    return ({"value": n / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+             "sample": f"the first {n} of the {len(Q)} test queries at L={L}, k=10, "
+                       f"{len(chunks)} chunks on {cores} threads"}, ref)
+
+
+def _parity(gpu_out, ref):
+    """Timed GPU results against the oracle's, query by query: ids, visits,
+    hops and status exact, distances within 1e-6 relative."""
+    n = ref[0].shape[0]
+    ids = gpu_out[0][:n].cpu().numpy().view(np.uint32)
+    dist = gpu_out[1][:n].cpu().numpy()
+    vis = gpu_out[2][:n].cpu().numpy().view(np.uint32)
+    hops = gpu_out[3][:n].cpu().numpy().view(np.uint32)
+    st = gpu_out[4][:n].cpu().numpy()
+    bad = ~np.all(ids == ref[0], axis=1)
+    bad |= (vis != ref[2]) | (hops != ref[3]) | (st != ref[4])
+    fin = np.isfinite(ref[1])
+    derr = np.where(fin, np.abs(dist.astype(np.float64) - ref[1]) / np.maximum(np.abs(ref[1]), 1e-30), 0.0)
+    bad |= np.any(derr > 1e-6, axis=1) | np.any(np.isfinite(dist) != fin, axis=1)
+    return {"checked": int(n), "mismatches": int(bad.sum()),
+            "compared": "ids, visits, hops, status exact; distances within 1e-6 relative",
+            "against": "oracle.beam_search on the timed index and queries", "max_rel_dist_err": float(derr.max())}
+
+
+def _gt_check(X, Q, gt, n_sample=1000, k=10):
+    """The recall ground truth (the library's kNN) against the oracle's FP64
+    brute force on sampled test queries. A row passes when every returned id's
+    FP64 distance is within 1e-5 of the FP64 k-th best (a different id there
+    can only come from a near-tie in FP32)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    rows = np.sort(np.random.default_rng(17).choice(Q.shape[0], min(n_sample, Q.shape[0]), replace=False))
+    cores = os.cpu_count() or 1
+    chunks = [c for c in np.array_split(rows, cores * 2) if len(c)]
+    t0 = time.time()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        parts = list(ex.map(lambda ix: oracle.knn_f64(Q[ix], X, k), chunks))
+    ref_ids = np.concatenate([p[0] for p in parts])
+    ref_d = np.concatenate([p[1] for p in parts])
+    exact = near_tie = bad = 0
+    for j, r in enumerate(rows):
+        g = gt[r, :k]
+        if np.array_equal(np.sort(g), np.sort(ref_ids[j])):
+            exact += 1
+            continue
+        d64 = -(X[g].astype(np.float64) @ Q[r].astype(np.float64))
+        if np.all(d64 <= ref_d[j, k - 1] + 1e-5):
+            near_tie += 1
+        else:
+            bad += 1
+    return {"checked": int(len(rows)), "same_set": exact, "differ_only_at_near_ties": near_tie,
+            "mismatches": bad, "against": f"oracle.knn_f64 (FP64 brute force) top-{k}",
+            "seconds": round(time.time() - t0, 1)}
 
 
 def _serve_rate(srv, Qpool, rate, duration, seed_tag):
@@ -428,66 +482,46 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
             gidx.close()
         res.update({"graphs": table, "build_id_graph": st_id})
     elif args.mode == "ablation":
-        # Sec. 5.4: search the bipartite graph G_bi (base and training-query
-        # nodes), the projected graph G_pj and the final RoarGraph with the
-        # same OOD queries. G_bi: base x -> every training query whose nearest
-        # base row is x (at most 128 kept), query t -> its other N_q - 1
-        # nearest base rows; query nodes are searched like base rows and
-        # dropped from the answers.
+        # Sec. 5.4: search the bipartite graph G_bi (Alg. 1's bipartite step,
+        # every x -> t edge kept, searched through query nodes as in Sec. 4.1),
+        # the projected graph G_pj and the final RoarGraph with the same OOD
+        # queries.
         t0 = time.time()
         T = rs.train_queries(w)
         Td = torch.from_numpy(T).to(dev)
         del T
         adj_f, entry_f, st_f, pj = pkg.build_index(Xd, Td, nq_depth=100, M=32, L_build=500, return_pj=True)
         kid, _ = pkg.knn(Td, Xd, 100)
-        torch.cuda.synchronize()
-        knn_h = kid.cpu().numpy().view(np.uint32)
-        del kid
-        n, nt = w.n, Td.shape[0]
-        RB = 128
-        piv = knn_h[:, 0].astype(np.int64)
-        order = np.argsort(piv, kind="stable")
-        ps = piv[order]
-        start = np.searchsorted(ps, np.arange(n))
-        rank = np.arange(nt) - start[ps]
-        keep = rank < RB
-        adj_bi = np.full((n + nt, RB), 0xFFFFFFFF, dtype=np.uint32)
-        adj_bi[ps[keep], rank[keep]] = (n + order[keep]).astype(np.uint32)
-        adj_bi[n:, :knn_h.shape[1] - 1] = knn_h[:, 1:]
-        Xbi = torch.cat([Xd, Td])
-        # The medoid is usually no pivot, so it has no out-edge in G_bi: start
-        # G_bi searches at the training-query node nearest to it instead.
-        qe, _ = pkg.knn(Xd[entry_f:entry_f + 1].contiguous(), Td, 1)
-        entry_bi = n + int(qe.cpu().numpy().view(np.uint32)[0, 0])
         del Td
-        adj_bi_d = torch.from_numpy(adj_bi.view(np.int32)).to(dev)
-        log(f"graphs ready in {time.time() - t0:.1f}s")
-        graphs = {"G_bi": (Xbi, adj_bi_d, True, entry_bi), "G_pj": (Xd, pj, False, entry_f),
-                  "RoarGraph": (Xd, adj_f, False, entry_f)}
+        off, qids, nout, bst = pkg.bipartite(kid, w.n)
+        del kid
+        # G_bi's entry: the medoid when it has a query out-neighbour, else the
+        # base node with one nearest to it (FP64 inner product, ties by id).
+        offh = off.cpu().numpy()
+        entry_bi = entry_f
+        if offh[entry_f + 1] == offh[entry_f]:
+            piv = np.nonzero(np.diff(offh) > 0)[0]
+            sc = X[piv].astype(np.float64) @ X[entry_f].astype(np.float64)
+            entry_bi = int(piv[np.lexsort((piv, -sc))[0]])
+        log(f"graphs ready in {time.time() - t0:.1f}s; G_bi {bst}")
+        graphs = {"G_bi": pkg.BipartiteIndex(Xd, nout, off, qids, entry_bi, max_visits=16384),
+                  "G_pj": pkg.Index(Xd, pj, entry_f, max_visits=16384),
+                  "RoarGraph": pkg.Index(Xd, adj_f, entry_f, max_visits=16384)}
         table = {}
-        for gname, (Xg, ag, has_q, eg) in graphs.items():
-            gidx = pkg.Index(Xg, ag, eg, max_visits=16384)
+        for gname, gidx in graphs.items():
             rows = {}
             for L in (10, 20, 50, 100, 200, 500):
-                kq = L if has_q else 10
-                ms = _time_once(lambda: gidx.search(Qd, kq, L), torch)
-                ids, dist, visits, hops, st = gidx.search(Qd, kq, L)
+                ms = _time_once(lambda: gidx.search(Qd, 10, L), torch)
+                ids, dist, visits, hops, st = gidx.search(Qd, 10, L)
                 torch.cuda.synchronize()
-                ih = ids.cpu().numpy().view(np.uint32)
-                if has_q:   # first 10 base ids of each answer
-                    base = np.full((ih.shape[0], 10), 0xFFFFFFFF, dtype=np.uint32)
-                    for i in range(ih.shape[0]):
-                        b = ih[i][ih[i] < n][:10]
-                        base[i, :len(b)] = b
-                    ih = base
-                rows[str(L)] = {"recall_at_10": _recall(ih, gt), "visits": float(visits.double().mean()),
-                                "hops": float(hops.double().mean()),
-                                "visits_per_hop": float(visits.double().mean() / max(hops.double().mean(), 1.0)),
-                                "qps": nq / (ms / 1e3)}
+                rows[str(L)] = {"recall_at_10": _recall(ids.cpu().numpy().view(np.uint32), gt),
+                                "visits": float(visits.double().mean()), "hops": float(hops.double().mean()),
+                                "visits_per_hop": float(visits.double().sum() / max(hops.double().sum(), 1.0)),
+                                "capped": int((st == 4).sum()), "qps": nq / (ms / 1e3)}
             gidx.close()
             table[gname] = rows
             log(f"{gname}: {rows}")
-        res.update({"graphs": table, "g_bi_rows": int(n + nt), "g_bi_query_edges_capped": int((~keep).sum()),
+        res.update({"graphs": table, "g_bi": {**bst, "entry": entry_bi, "query_nodes": int(qids.shape[0])},
                     "build": st_f})
     elif args.mode == "update":
         # Sec. 5.7: insertion through the saved bipartite graph, and deletion by
@@ -593,6 +627,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override base rows (smaller runs)")
     ap.add_argument("--n-train", type=int, default=0, help="override training queries")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--n-comp", type=int, default=0, help="override the mixture components (small experiments)")
     ap.add_argument("--offset-norm", type=float, default=0.0,
                     help="override the OOD offset norm (ood mode experiments; the workloads use 1.5)")
     ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving", "ood", "ablation", "update"],
@@ -632,6 +667,8 @@ def main():
         w = rs.scaled(w, n_train=args.n_train)
     if args.offset_norm > 0:
         w = rs.scaled(w, offset_norm=args.offset_norm)
+    if args.n_comp > 0:
+        w = rs.scaled(w, n_comp=args.n_comp)
     dev, X, Q, Xd, Qd, adj, entry, gt, bstats = _setup(w, torch, pkg, rs, log)
     if args.mode != "main":
         out = _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bstats, log)
@@ -641,7 +678,7 @@ def main():
     sweep = _sweep(idx, Qd, gt, torch, L_SWEEP)
     L, reached = _pick_L(sweep)
     log(f"sweep {json.dumps(sweep)} -> L={L}")
-    best, tune_ms = idx.autotune(Qd, 10, L, repeats=2)
+    best, tune_ms = (-1, []) if args.impl == "reference" else idx.autotune(Qd, 10, L, repeats=2)
     log(f"autotune L={L}: best variant {best}, ms {[round(float(x), 3) for x in tune_ms]}")
     nq = Q.shape[0]
     config = {"workload": f"{w.name}: base {w.n}x{w.d} FP32, {w.n_train} training + {nq} test OOD queries, "
@@ -656,7 +693,7 @@ def main():
         adj_np = adj.cpu().numpy().view(np.uint32)
         step_s = []
         for _ in range(args.warmup + args.steps):
-            cb = _cpu_baseline(X, adj_np, entry, Q, L, budget_s=max(1.0, 60.0 / (args.steps + args.warmup)))
+            cb, _ = _cpu_baseline(X, adj_np, entry, Q, L, budget_s=max(1.0, 60.0 / (args.steps + args.warmup)))
             step_s.append(cb)
         vals = [c["value"] for c in step_s[args.warmup:]]
         v = statistics.median(vals)
@@ -779,9 +816,11 @@ def main():
         srv.close()
         sidx.close()
 
-    cpu = None
+    cpu = parity = gt_check = None
     if rank == 0:
-        cpu = _cpu_baseline(X, adj.cpu().numpy().view(np.uint32), entry, Q, L)
+        cpu, ref = _cpu_baseline(X, adj.cpu().numpy().view(np.uint32), entry, Q, L)
+        parity = _parity(out, ref)
+        gt_check = _gt_check(X, Q, gt)
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -797,6 +836,8 @@ def main():
                      "peak_source": f"{peak_src} hbm_gbs (burst copy)",
                      "bytes_per_query": bytes_q, "kernel": "beam_search_kernel<f32>"},
         "cpu_baseline": cpu,
+        "parity": parity,
+        "ground_truth_check": gt_check,
         "clocks": clk.summary(),
         "forms": forms,
         "uneven": uneven,
@@ -809,6 +850,10 @@ def main():
     idx.close()
     if dist_on:
         tdist.destroy_process_group()
+    if rank == 0 and (parity["mismatches"] or gt_check["mismatches"]):
+        print(f"parity failure: {parity['mismatches']} searched queries differ from the oracle, "
+              f"{gt_check['mismatches']} ground-truth rows differ from FP64 brute force", file=sys.stderr)
+        sys.exit(1)
 
 
 if __name__ == "__main__":

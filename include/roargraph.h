@@ -57,7 +57,7 @@ typedef struct roar_server roar_server;
 /* Serving-loop configuration (roar_server_create). */
 typedef struct {
     int32_t ring_capacity;  /* query slots that may be in flight; 0: from memory_budget */
-    int64_t memory_budget;  /* bytes of in-flight state when ring_capacity == 0 (0: 65536 slots) */
+    int64_t memory_budget;  /* bytes of in-flight requests (see roar_server_create); 0: no byte limit */
     int32_t k_max;          /* largest k of a request */
     int32_t L_max;          /* largest L of a request (sizes each team's pool) */
     int32_t team_warps;     /* warps per query team, 0: the handle's tuning for L_max */
@@ -98,6 +98,44 @@ const char *roar_last_error(void);
 roar_status roar_index_create(int64_t n, int32_t d, const float *base_f32, roar_dtype trav_dtype,
                               const void *base_trav, const float *scales, const uint32_t *adj,
                               int32_t rmax, uint32_t entry, uint32_t max_visits, roar_index **out);
+
+/*
+ * The query-base bipartite graph G_bi of Alg. 1 (Sec. 4.2.2) from the
+ * training queries' kNN lists: query node t has out-edges to its N_q - 1
+ * nearest base rows after the first (N_out(t)); the nearest, x, gets the
+ * out-edge x -> t. Every such edge is kept (no degree bound on B(x)).
+ *   knn    device [nt][nqd] uint32, each row the training query's nqd nearest
+ *          base ids in rank order (roar_knn), 2 <= nqd <= ROAR_MAX_RMAX + 1.
+ *   off    device [n + 1] int64 out: B(x) = qids[off[x] .. off[x + 1]).
+ *   qids   device [nt] uint32 out: query ids grouped by base node, ascending.
+ *   nout   device [nt][nqd - 1] uint32 out: N_out(t) (knn without column 0).
+ *   stats  host [2] out or NULL: base nodes with a query out-neighbour,
+ *          largest |B(x)|.
+ * Builds the CSR on the host (a counting sort of the nt rank-0 ids) and
+ * synchronises `stream`. Errors: ROAR_EINVAL (also for an id >= n),
+ * ROAR_ECUDA.
+ */
+roar_status roar_bipartite(const uint32_t *knn, int64_t nt, int32_t nqd, int64_t n, int64_t *off,
+                           uint32_t *qids, uint32_t *nout, int64_t *stats, void *stream);
+
+/*
+ * A search handle over G_bi (roar_bipartite), for the ablation of Sec. 5.4:
+ * roar_search on it runs the greedy search on the bipartite graph described
+ * in Sec. 4.1, from a base node through its query out-neighbours to their
+ * base out-neighbours. Only base nodes enter the pool and are scored (FP32,
+ * the search's fixed order); expanding base node v scans N_out(t) for every
+ * t in B(v), ascending, and the visit cap is checked before each such list.
+ * Hops count expanded base nodes, visits count scored base nodes.
+ *   n, d, base_f32, entry, max_visits   as roar_index_create (FP32 only).
+ *   nout [nt][rn], bi_off [n + 1], bi_q [nt]   device arrays from roar_bipartite
+ *                                              (rn = nqd - 1), borrowed.
+ * The handle searches with one warp per query (roar_index_set_tuning with
+ * more warps makes its searches fail with ROAR_EINVAL).
+ * Errors: as roar_index_create.
+ */
+roar_status roar_index_create_bipartite(int64_t n, int32_t d, const float *base_f32, const uint32_t *nout,
+                                        int32_t rn, int64_t nt, const int64_t *bi_off, const uint32_t *bi_q,
+                                        uint32_t entry, uint32_t max_visits, roar_index **out);
 
 /* Release a handle and its scratch (synchronises the device first). NULL is ignored. */
 void roar_index_destroy(roar_index *idx);
@@ -263,9 +301,20 @@ roar_status roar_search_noalloc(int64_t n, int32_t d, const float *base_f32, con
  * published, so requests that arrive while others run start as soon as a
  * team is free. Every query is the beam search of roar_search with its
  * request's k and L, bit-identical to searching it alone.
- * Admission: the ring holds ring_capacity queries (or memory_budget / (4d +
- * 8 k_max + 8 L_max + 24) when 0); a request that does not fit is refused
- * with ROAR_EBUSY and may be retried after polls release slots.
+ * Admission, by memory: a query at (k, L) is charged
+ *   4 d + 8 k + 24          its ring slot at its own k (query, results, counters)
+ *   + 8 L                   its candidate pool
+ *   + 4 * 2^ceil(log2(32 L)) the exact visited table for a beam of width L
+ *                           (the kernel's sizing rule for its shared table)
+ * bytes; a request of nq queries is charged nq times that. With
+ * memory_budget > 0 a request is admitted only while the charges of the
+ * requests in flight (submitted, not yet released by a poll) plus its own
+ * stay within the budget; it is refused with ROAR_EBUSY otherwise and may be
+ * retried after polls release requests (a request whose charge exceeds the
+ * whole budget, or with more queries than ring slots, is ROAR_EINVAL). The
+ * ring holds ring_capacity query slots of k_max results each (0: as many as
+ * memory_budget / (4 d + 8 k_max + 24) allows, at most 2^26, or 65536 without
+ * a budget); a request also needs free slots for all its queries.
  * The kernel's teams exit after idle_ms without work and the server
  * relaunches it when work is waiting; every wait in the kernel is bounded.
  * The server uses the handle's scratch: do not search the same handle while
@@ -290,8 +339,9 @@ roar_status roar_server_submit(roar_server *srv, const float *q_host, int32_t nq
 roar_status roar_server_poll(roar_server *srv, uint64_t request_id, int32_t timeout_ms, uint32_t *ids,
                              float *dist, uint32_t *visits, int32_t *qstatus, double *latency_s);
 
-/* out[8]: ring capacity, queries submitted, completed, released, kernel
- * launches, CTAs per launch, warps per team, kernel running (0/1). */
+/* out[10]: ring capacity, queries submitted, completed, released, kernel
+ * launches, CTAs per launch, warps per team, kernel running (0/1), bytes
+ * charged to requests in flight, memory budget. */
 roar_status roar_server_stats(roar_server *srv, double *out);
 
 /* Stop the kernel (bounded), join the poller and free the server. NULL is ignored. */

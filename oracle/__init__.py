@@ -22,6 +22,10 @@ Parity status of each function:
 * ``repair`` (reachability repair, an addition) -- pinned (hand-traced case
   ``repair_circle.json``).
 * ``insert`` (Sec. 5.7) -- pinned (hand-traced case ``insertion_circle.json``).
+* ``bipartite`` / ``beam_search_bi`` (G_bi of Alg. 1, searched through query
+  nodes as in Sec. 4.1; the ablation of Sec. 5.4) -- pinned (hand-traced case
+  ``bipartite_search.json``, and on a complete bipartite graph the search
+  equals brute force).
 """
 from __future__ import annotations
 
@@ -96,6 +100,10 @@ def _load():
         lib.orc_acquire_neighbors_f32.restype = i32
         lib.orc_insert.argtypes = [P, i64, i32, P, i32, u32, i64, P, i64, P, P, P, i32, i32, i32, u32, P]
         lib.orc_insert.restype = i32
+        lib.orc_bipartite.argtypes = [P, i64, i32, i64, P, P]
+        lib.orc_bipartite.restype = ctypes.c_int
+        lib.orc_beam_search_bi.argtypes = [P, i64, i32, P, i64, i32, u32, P, i64, i32, i32, u32, P, P, P, P, P]
+        lib.orc_beam_search_bi.restype = ctypes.c_int
         lib.orc_repair.argtypes = [P, i64, i32, P, i32, u32, P]
         lib.orc_repair.restype = i64
         lib.orc_build.argtypes = [P, i64, i64, i32, P, i32, i32, i32, u32, P, P, P]
@@ -301,6 +309,41 @@ def beam_search(X32, adj, entry: int, Q, k: int, L: int, max_visits: int = 1 << 
                                       _p(visits), _p(hops), _p(status))
     if rc != 0:
         raise ValueError(f"orc_beam_search failed: {rc}")
+    return ids, dist, visits, hops, status
+
+
+def bipartite(knn_ids, n: int):
+    """G_bi of Alg. 1 as CSR: (off [n+1] int64, qids [nt] uint32), B(x) =
+    qids[off[x]:off[x+1]] = every training query whose nearest base row is x,
+    ascending. N_out(t) is knn_ids[t, 1:]."""
+    knn_ids = np.ascontiguousarray(knn_ids, dtype=np.uint32)
+    nt, nqd = knn_ids.shape
+    off = np.empty(n + 1, dtype=np.int64)
+    qids = np.empty(max(nt, 1), dtype=np.uint32)
+    rc = _load().orc_bipartite(_p(knn_ids), nt, nqd, n, _p(off), _p(qids))
+    if rc != 0:
+        raise ValueError(f"orc_bipartite failed: {rc}")
+    return off, qids[:nt]
+
+
+def beam_search_bi(X, knn_ids, entry: int, Q, k: int, L: int, max_visits: int = 1 << 20):
+    """Beam search on G_bi (base nodes scored, routed through query nodes; see
+    roar_oracle.c). Returns ids, dist, visits, hops, status as beam_search."""
+    X = _f32(X)
+    knn_ids = np.ascontiguousarray(knn_ids, dtype=np.uint32)
+    Q = _f32(Q).reshape(-1, X.shape[1])
+    n, d = X.shape
+    nt, nqd = knn_ids.shape
+    nq = Q.shape[0]
+    ids = np.empty((nq, k), dtype=np.uint32)
+    dist = np.empty((nq, k), dtype=np.float32)
+    visits = np.empty(nq, dtype=np.uint32)
+    hops = np.empty(nq, dtype=np.uint32)
+    status = np.empty(nq, dtype=np.int32)
+    rc = _load().orc_beam_search_bi(_p(X), n, d, _p(knn_ids), nt, nqd, entry, _p(Q), nq, k, L, max_visits,
+                                    _p(ids), _p(dist), _p(visits), _p(hops), _p(status))
+    if rc != 0:
+        raise ValueError(f"orc_beam_search_bi failed: {rc}")
     return ids, dist, visits, hops, status
 
 

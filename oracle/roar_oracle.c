@@ -385,6 +385,112 @@ int orc_beam_search_trace(const float *X, int64_t n, int32_t d, const uint32_t *
 }
 
 /* ------------------------------------------------------------------------ */
+/* Search on the query-base bipartite graph G_bi (Alg. 1 bipartite step,     */
+/* searched as in Sec. 4.1 and the ablation of Sec. 5.4).                    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * G_bi from the training queries' kNN lists knn [nt][nqd] (rank order):
+ * query node t has out-edges to knn[t][1..nqd-1] (N_out(t), the edge to its
+ * nearest base node removed), and that nearest base node x = knn[t][0] has
+ * the out-edge x -> t. Every such edge is kept: B(x) lists all t with
+ * knn[t][0] = x, in ascending t. Written as CSR: off [n+1], qids [nt].
+ */
+int orc_bipartite(const uint32_t *knn, int64_t nt, int32_t nqd, int64_t n, int64_t *off, uint32_t *qids) {
+    if (nt < 0 || nqd < 1 || n < 1) return ORC_EINVAL;
+    for (int64_t x = 0; x <= n; ++x) off[x] = 0;
+    for (int64_t t = 0; t < nt; ++t) {
+        if ((int64_t)knn[t * nqd] >= n) return ORC_EINVAL;
+        ++off[knn[t * nqd] + 1];
+    }
+    for (int64_t x = 0; x < n; ++x) off[x + 1] += off[x];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!fill) return ORC_ENOMEM;
+    for (int64_t x = 0; x < n; ++x) fill[x] = off[x];
+    for (int64_t t = 0; t < nt; ++t) qids[fill[knn[t * nqd]]++] = (uint32_t)t;   /* ascending t */
+    free(fill);
+    return ORC_OK;
+}
+
+/*
+ * Beam search on G_bi (FP32 fixed-order distances). A greedy search on the
+ * bipartite graph goes from a base node to its query out-neighbours and on
+ * to their base out-neighbours (Sec. 4.1), so only base nodes enter the pool
+ * and are scored: expanding base node v scans, for each t in B(v) in
+ * ascending order, N_out(t) in rank order, visiting and scoring every base
+ * node not yet visited. The visit cap is checked before each query node's
+ * list is scanned (visits >= max_visits stops the search with status 4).
+ * Everything else (pool, order, termination, output) is the beam search of
+ * search_one. Returns status; results as orc_beam_search with dtype 0.
+ */
+int orc_beam_search_bi(const float *X, int64_t n, int32_t d, const uint32_t *knn, int64_t nt, int32_t nqd,
+                       uint32_t entry, const float *Q, int64_t nq, int32_t k, int32_t L, uint32_t max_visits,
+                       uint32_t *ids, float *dist, uint32_t *visits, uint32_t *hops, int32_t *qstatus) {
+    if (n < 1 || d < 1 || nqd < 2 || (int64_t)entry >= n || k < 1 || L < k || nq < 0) return ORC_EINVAL;
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    uint32_t *qids = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nt > 0 ? nt : 1));
+    ent32 *pool = (ent32 *)malloc(sizeof(ent32) * (size_t)L);
+    unsigned char *visited = (unsigned char *)malloc((size_t)n);
+    int rc = ORC_ENOMEM;
+    if (!off || !qids || !pool || !visited) goto done;
+    rc = orc_bipartite(knn, nt, nqd, n, off, qids);
+    if (rc != ORC_OK) goto done;
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        const float *q = Q + qi * d;
+        int st = ORC_OK;
+        int32_t size = 0;
+        uint32_t nvis = 1, nh = 0;
+        memset(visited, 0, (size_t)n);
+        visited[entry] = 1;
+        pool_insert32(pool, &size, L, -orc_dot_fixed(q, X + (int64_t)entry * d, d), entry);
+        for (;;) {
+            int32_t sel = -1;
+            for (int32_t i = 0; i < size; ++i)
+                if (!pool[i].checked) { sel = i; break; }
+            if (sel < 0) break;
+            if (nvis >= max_visits) { st = ORC_EOVERFLOW; break; }
+            pool[sel].checked = 1;
+            const uint32_t v = pool[sel].id;
+            ++nh;
+            int stop = 0;
+            for (int64_t j = off[v]; j < off[v + 1] && !stop; ++j) {
+                if (nvis >= max_visits) { st = ORC_EOVERFLOW; stop = 1; break; }
+                const uint32_t *nout = knn + (int64_t)qids[j] * nqd + 1;
+                for (int32_t r = 0; r < nqd - 1; ++r) {
+                    const uint32_t u = nout[r];
+                    if (u == ORC_NONE) continue;
+                    if ((int64_t)u >= n) { st = ORC_EINVAL; continue; }
+                    if (visited[u]) continue;
+                    visited[u] = 1;
+                    ++nvis;
+                    pool_insert32(pool, &size, L, -orc_dot_fixed(q, X + (int64_t)u * d, d), u);
+                }
+            }
+            if (stop) break;
+        }
+        int32_t r = 0;
+        for (; r < size && r < k; ++r) {
+            ids[qi * k + r] = pool[r].id;
+            dist[qi * k + r] = pool[r].d;
+        }
+        for (; r < k; ++r) {
+            ids[qi * k + r] = ORC_NONE;
+            dist[qi * k + r] = INFINITY;
+        }
+        if (visits) visits[qi] = nvis;
+        if (hops) hops[qi] = nh;
+        if (qstatus) qstatus[qi] = st;
+    }
+    rc = ORC_OK;
+done:
+    free(off);
+    free(qids);
+    free(pool);
+    free(visited);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact kNN (Definition 1, Sec. 2.1.1) in FP64, ties to the lower id.       */
 /* ------------------------------------------------------------------------ */
 

@@ -53,6 +53,10 @@ def lib() -> ctypes.CDLL:
     L.roar_index_create.argtypes = [i64, i32, P, ctypes.c_int, P, P, P, i32, u32, u32,
                                     ctypes.POINTER(P)]
     L.roar_index_create.restype = ctypes.c_int
+    L.roar_index_create_bipartite.argtypes = [i64, i32, P, P, i32, i64, P, P, u32, u32, ctypes.POINTER(P)]
+    L.roar_index_create_bipartite.restype = ctypes.c_int
+    L.roar_bipartite.argtypes = [P, i64, i32, i64, P, P, P, P, P]
+    L.roar_bipartite.restype = ctypes.c_int
     L.roar_index_set_hash_log2.argtypes = [P, i32]
     L.roar_index_set_hash_log2.restype = ctypes.c_int
     L.roar_index_set_tombstones.argtypes = [P, P]
@@ -119,6 +123,18 @@ def roar_index_create(n, d, base_f32, trav_dtype, base_trav, scales, adj, rmax, 
     _check(lib().roar_index_create(n, d, base_f32, trav_dtype, base_trav, scales, adj, rmax,
                                    entry, max_visits, ctypes.byref(h)), "roar_index_create")
     return h.value
+
+
+def roar_index_create_bipartite(n, d, base_f32, nout, rn, nt, bi_off, bi_q, entry, max_visits=0):
+    """Raw C-ABI call (pointer arguments are device addresses)."""
+    h = ctypes.c_void_p()
+    _check(lib().roar_index_create_bipartite(n, d, base_f32, nout, rn, nt, bi_off, bi_q, entry, max_visits,
+                                             ctypes.byref(h)), "roar_index_create_bipartite")
+    return h.value
+
+
+def roar_bipartite(knn, nt, nqd, n, off, qids, nout, stats=None, stream=None):
+    _check(lib().roar_bipartite(knn, nt, nqd, n, off, qids, nout, stats, stream), "roar_bipartite")
 
 
 def roar_index_set_tombstones(idx, bits):
@@ -193,13 +209,22 @@ def roar_server_create(handle, cfg):
 
 
 def roar_server_submit(srv, q_host, nq, k, L):
-    """Returns the request id, or None when the ring has no room (ROAR_EBUSY)."""
+    """Returns the request id, or None when admission refuses it now (ROAR_EBUSY)."""
     rid = ctypes.c_uint64()
     st = lib().roar_server_submit(srv, q_host, nq, k, L, ctypes.byref(rid))
     if st == ROAR_EBUSY:
         return None
     _check(st, "roar_server_submit")
     return rid.value
+
+
+def server_query_charge(d, k, L):
+    """Bytes one query at (k, L) is charged by the serving loop's admission
+    (include/roargraph.h, roar_server_create)."""
+    lg = 0
+    while (1 << lg) < 32 * L:
+        lg += 1
+    return 4 * d + 8 * k + 24 + 8 * L + (4 << lg)
 
 
 def roar_server_poll(srv, request_id, timeout_ms, ids=None, dist=None, visits=None, qstatus=None):
@@ -215,10 +240,10 @@ def roar_server_poll(srv, request_id, timeout_ms, ids=None, dist=None, visits=No
 def roar_server_stats(srv):
     import numpy as np
 
-    out = np.zeros(8, dtype=np.float64)
+    out = np.zeros(10, dtype=np.float64)
     _check(lib().roar_server_stats(srv, out.ctypes.data), "roar_server_stats")
     return dict(zip(["ring", "submitted", "completed", "released", "launches", "blocks", "team_warps",
-                     "running"], out.tolist()))
+                     "running", "inflight_bytes", "memory_budget"], out.tolist()))
 
 
 def roar_server_destroy(srv):
@@ -389,6 +414,44 @@ class Index:
         return out
 
 
+class BipartiteIndex(Index):
+    """A search handle over the bipartite graph G_bi (see bipartite()): the
+    greedy search through query nodes of Sec. 4.1, for the ablation of
+    Sec. 5.4. Searches like Index (FP32, one warp per query)."""
+
+    def __init__(self, base_f32, nout, off, qids, entry, max_visits=0):
+        import torch
+
+        assert base_f32.is_cuda and base_f32.dtype == torch.float32 and base_f32.is_contiguous()
+        assert nout.is_cuda and nout.dtype == torch.int32 and nout.is_contiguous()
+        assert off.dtype == torch.int64 and qids.dtype == torch.int32
+        self.base_f32, self.adj, self.trav, self.scales = base_f32, nout, None, None
+        self.off, self.qids = off, qids
+        self.n, self.d = base_f32.shape
+        self.rmax = nout.shape[1]
+        self.entry = int(entry)
+        self.dtype = "f32"
+        self.handle = roar_index_create_bipartite(self.n, self.d, _ptr(base_f32), _ptr(nout), self.rmax,
+                                                  nout.shape[0], _ptr(off), _ptr(qids), self.entry, max_visits)
+
+
+def bipartite(knn, n, stream=None):
+    """G_bi of Alg. 1 from CUDA int32 kNN lists [nt, nqd] over n base rows:
+    returns (off int64 [n+1], qids int32 [nt], nout int32 [nt, nqd-1], stats)."""
+    import numpy as np
+    import torch
+
+    assert knn.is_cuda and knn.dtype == torch.int32 and knn.is_contiguous()
+    nt, nqd = knn.shape
+    dev = knn.device
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    qids = torch.empty(nt, dtype=torch.int32, device=dev)
+    nout = torch.empty((nt, nqd - 1), dtype=torch.int32, device=dev)
+    st = np.zeros(2, dtype=np.int64)
+    roar_bipartite(_ptr(knn), nt, nqd, n, _ptr(off), _ptr(qids), _ptr(nout), st.ctypes.data, _stream_ptr(stream))
+    return off, qids, nout, {"base_nodes_with_query_edges": int(st[0]), "widest_base_row": int(st[1])}
+
+
 STAT_KEYS = ["total_s", "knn_s", "projection_s", "enhance_search_s", "reverse_merge_s", "repair_s",
              "pivots", "pj_edges", "final_edges", "unreachable_before_repair", "repairs",
              "unreachable_after_repair"]
@@ -506,7 +569,8 @@ class Server:
         self.d = index.d
 
     def submit(self, q, k, L):
-        """q: float32 numpy [nq, d]; returns a request id or None if the ring is full."""
+        """q: float32 numpy [nq, d]; returns a request id, or None when admission
+        refuses it now (no free slots, or its memory charge does not fit)."""
         import numpy as np
 
         q = np.ascontiguousarray(q, dtype=np.float32)

@@ -43,6 +43,11 @@ struct roar_index {
     const float *scales;
     const uint32_t *adj;
     const uint32_t *tomb = nullptr;  // caller-owned deletion bitmap or null
+    // Bipartite graph G_bi (null for a plain graph): `adj` holds N_out rows of
+    // bi_nt query nodes, B(x) = bi_q[bi_off[x] .. bi_off[x + 1]).
+    const int64_t *bi_off = nullptr;
+    const uint32_t *bi_q = nullptr;
+    int64_t bi_nt = 0;
     int32_t rmax;
     uint32_t entry;
     uint32_t max_visits;
@@ -154,6 +159,26 @@ extern "C" roar_status roar_index_create(int64_t n, int32_t d, const float *base
     return ROAR_OK;
 }
 
+extern "C" roar_status roar_index_create_bipartite(int64_t n, int32_t d, const float *base_f32,
+                                                   const uint32_t *nout, int32_t rn, int64_t nt,
+                                                   const int64_t *bi_off, const uint32_t *bi_q, uint32_t entry,
+                                                   uint32_t max_visits, roar_index **out) {
+    if (!out) return ROAR_EINVAL;
+    *out = nullptr;
+    if (nt < 1 || nt >= (int64_t)kIdMask || !bi_off || !bi_q || !aligned(bi_off, 8) || !aligned(bi_q, 4)) {
+        set_error("roar_index_create_bipartite: bad query-node count or CSR arrays");
+        return ROAR_EINVAL;
+    }
+    roar_index *idx = nullptr;
+    roar_status st = roar_index_create(n, d, base_f32, ROAR_F32, nullptr, nullptr, nout, rn, entry, max_visits, &idx);
+    if (st != ROAR_OK) return st;
+    idx->bi_off = bi_off;
+    idx->bi_q = bi_q;
+    idx->bi_nt = nt;
+    *out = idx;
+    return ROAR_OK;
+}
+
 extern "C" roar_status roar_index_set_hash_log2(roar_index *idx, int32_t log2) {
     if (!idx || (log2 != 0 && log2 != -1 && (log2 < 5 || log2 > 15))) {
         set_error("roar_index_set_hash_log2: log2 must be 0, -1 or in [5, 15]");
@@ -237,8 +262,16 @@ roar_status plan_search(roar_index *idx, int32_t lmax, SearchArgs &a, int &block
     a.lcap = (lmax + 31) / 32 * 32;
     a.max_visits = idx->max_visits;
     a.hash_log2 = t.hash == 0 ? hash_log2_for(lmax) : (t.hash < 0 ? 0 : t.hash);
+    a.bi_off = idx->bi_off;
+    a.bi_q = idx->bi_q;
+    a.bi_nt = idx->bi_nt;
+    const bool bi = idx->bi_off != nullptr;
     tw = t.tw;
-    int bps = search_blocks_per_sm((int)idx->dtype, idx->d, idx->rmax, a.lcap, a.hash_log2, tw);
+    if (bi && tw != 1) {
+        set_error("roar_search: the bipartite-graph search runs one warp per query");
+        return ROAR_EINVAL;
+    }
+    int bps = search_blocks_per_sm((int)idx->dtype, idx->d, idx->rmax, a.lcap, a.hash_log2, tw, bi);
     if (bps <= 0) {
         set_error("roar_search: this L does not fit in shared memory");
         return ROAR_EINVAL;

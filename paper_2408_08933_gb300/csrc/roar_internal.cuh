@@ -75,6 +75,12 @@ struct SearchArgs {
     uint32_t *visits;
     uint32_t *hops;
     int32_t *qstatus;
+    // Bipartite graph G_bi (null for a plain graph): expanding base node v
+    // scans, for each query node t in B(v) = bi_q[bi_off[v] .. bi_off[v+1]),
+    // the row t of `adj`, which then holds N_out(t) for bi_nt query nodes.
+    const int64_t *bi_off;
+    const uint32_t *bi_q;
+    int64_t bi_nt;
 };
 
 // Shared memory of one warp: pool (8 B per slot), candidate buffers (16 B per
@@ -146,11 +152,12 @@ __host__ __device__ inline size_t search_smem_per_team(int lcap, int hash_log2, 
 }
 // Resident CTAs per SM for this configuration with teams of tw warps (0 if it
 // cannot launch), the teams per CTA, and the launch itself.
-int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, int tw);
+int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, int tw, bool bi = false);
 int teams_per_block(int tw);
 cudaError_t launch_search(const SearchArgs &a, int blocks, int tw, cudaStream_t s, bool configure = true);
 template <int DT>
 const void *kernel_table(int nch, int rpl, int tw, bool staged);
+const void *kernel_table_bi(int nch, int rpl);
 
 int hash_log2_for(int L);
 

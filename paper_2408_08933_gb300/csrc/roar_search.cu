@@ -15,8 +15,9 @@ int threads_for(int tw) { return 32 * (tw > kWarpsPerBlock ? tw : kWarpsPerBlock
 
 int teams_per_block(int tw) { return threads_for(tw) / (32 * tw); }
 
-const void *search_kernel(int dtype, int d, int rmax, int tw, int lcap) {
+const void *search_kernel(int dtype, int d, int rmax, int tw, int lcap, bool bi = false) {
     const int nch = nch_for(d), rpl = rmax <= 64 ? 2 : 4;
+    if (bi) return (dtype == 0 && tw == 1) ? kernel_table_bi(nch, rpl) : nullptr;
     const bool staged = search_staged(dtype, d, tw, lcap);
     switch (dtype) {
         case 0: return kernel_table<0>(nch, rpl, tw, staged);
@@ -40,10 +41,11 @@ int hash_log2_for(int L) {
     return lg >= 9 ? lg : 0;
 }
 
-int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, int tw) {
-    const void *fn = search_kernel(dtype, d, rmax, tw, lcap);
+int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, int tw, bool bi) {
+    const void *fn = search_kernel(dtype, d, rmax, tw, lcap, bi);
     if (!fn) return 0;
-    const size_t smem = search_smem_per_team(lcap, hash_log2, search_stage_bytes(dtype, d, tw, lcap)) * teams_per_block(tw);
+    const size_t stage = bi ? 0 : search_stage_bytes(dtype, d, tw, lcap);
+    const size_t smem = search_smem_per_team(lcap, hash_log2, stage) * teams_per_block(tw);
     if (smem > 227 * 1024) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
@@ -55,10 +57,11 @@ int search_blocks_per_sm(int dtype, int d, int rmax, int lcap, int hash_log2, in
 }
 
 cudaError_t launch_search(const SearchArgs &a, int blocks, int tw, cudaStream_t s, bool configure) {
-    const void *fn = search_kernel(a.dtype, a.d, a.rmax, tw, a.lcap);
+    const bool bi = a.bi_off != nullptr;
+    const void *fn = search_kernel(a.dtype, a.d, a.rmax, tw, a.lcap, bi);
     if (!fn || blocks <= 0) return cudaErrorInvalidValue;
-    const size_t smem =
-        search_smem_per_team(a.lcap, a.hash_log2, search_stage_bytes(a.dtype, a.d, tw, a.lcap)) * teams_per_block(tw);
+    const size_t stage = bi ? 0 : search_stage_bytes(a.dtype, a.d, tw, a.lcap);
+    const size_t smem = search_smem_per_team(a.lcap, a.hash_log2, stage) * teams_per_block(tw);
     cudaError_t e = cudaSuccess;
     if (configure) {  // already done by search_blocks_per_sm when planning
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -415,9 +415,16 @@ struct TeamShape {
 // candidates of one hop.
 // STG > 0 (one warp per query): the hop's rows are gathered through shared
 // memory, STG rows per buffer (score_rows_staged).
-template <int DT, int NCH, int RPL, int TW, int STG>
+// BI (FP32, one warp): search on the bipartite graph G_bi. Expanding base
+// node v walks its query nodes t in B(v) and processes the row N_out(t) of
+// `adj` as one batch of candidates each (fetch, visited set, gather, merge)
+// before the next selection; by the invariant above this is the same pool as
+// merging all of v's two-hop neighbours at once. The visit cap is checked
+// before each query node's row.
+template <int DT, int NCH, int RPL, int TW, int STG, bool BI = false>
 __global__ void __launch_bounds__(TeamShape<DT, TW, STG>::kThreads, TeamShape<DT, TW, STG>::kMinBlocks)
 beam_search_kernel(const SearchArgs a) {
+    static_assert(!BI || (DT == 0 && TW == 1 && STG == 0), "bipartite search: FP32, one warp, register gather");
     constexpr int kMaxRowPerLane = RPL;
     constexpr int kMaxCandPerLane = RPL;
     constexpr int TPB = TeamShape<DT, TW>::kTeams;
@@ -523,6 +530,7 @@ beam_search_kernel(const SearchArgs a) {
             qr[c] = ch < d4 ? (serving ? __ldcv(q4 + ch) : __ldg(q4 + ch)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // Leader-only search state.
+        int64_t bi_j = 0, bi_end = 0;   // BI: query nodes of the base node being expanded
         int size = 1, cursor = 0, nlog = 0;
         uint32_t visits = 1, hops = 0, smem_count = 0;
         bool spilled = (H == 0), bad = false, overflow = false;
@@ -552,27 +560,55 @@ beam_search_kernel(const SearchArgs a) {
         for (;;) {
             int cnt = 0;
             if (leader) {
-                // Select: first unexpanded entry (all entries before `cursor` are expanded).
-                int sel = -1;
-                for (int b0 = cursor & ~31; b0 < size; b0 += 32) {
-                    const int i = b0 + lane;
-                    const bool open = i < size && !(pi[i] & kChecked);
-                    const unsigned m = __ballot_sync(kFull, open);
-                    if (m) {
-                        sel = b0 + __ffs(m) - 1;
-                        break;
+                uint32_t v = 0;        // the adjacency row to read this round
+                bool have_row = false;
+                if (BI && bi_j < bi_end) {
+                    // Next query node of the base node being expanded.
+                    if (visits >= a.max_visits) {
+                        overflow = true;
+                        cnt = -1;
+                    } else {
+                        v = a.bi_q[bi_j++];
+                        have_row = true;
+                    }
+                } else {
+                    // Select: first unexpanded entry (all entries before `cursor` are expanded).
+                    int sel = -1;
+                    for (int b0 = cursor & ~31; b0 < size; b0 += 32) {
+                        const int i = b0 + lane;
+                        const bool open = i < size && !(pi[i] & kChecked);
+                        const unsigned m = __ballot_sync(kFull, open);
+                        if (m) {
+                            sel = b0 + __ffs(m) - 1;
+                            break;
+                        }
+                    }
+                    if (sel >= 0 && visits >= a.max_visits) overflow = true;
+                    if (sel < 0 || overflow) {
+                        cnt = -1;
+                    } else {
+                        v = pi[sel] & kIdMask;
+                        __syncwarp();
+                        if (lane == 0) pi[sel] = v | kChecked;
+                        ++hops;
+                        cursor = sel + 1;
+                        if constexpr (BI) {
+                            bi_j = a.bi_off[v];
+                            bi_end = a.bi_off[v + 1];
+                            if (bi_j < bi_end) {
+                                v = a.bi_q[bi_j++];
+                                have_row = true;
+                            }
+                        } else {
+                            have_row = true;
+                        }
                     }
                 }
-                if (sel >= 0 && visits >= a.max_visits) overflow = true;
-                if (sel < 0 || overflow) {
-                    cnt = -1;
-                } else {
-                    const uint32_t v = pi[sel] & kIdMask;
-                    __syncwarp();
-                    if (lane == 0) pi[sel] = v | kChecked;
-                    ++hops;
-                    cursor = sel + 1;
-
+                if (BI && have_row && (int64_t)v >= a.bi_nt) {   // a query id past the N_out table
+                    bad = true;
+                    have_row = false;
+                }
+                if (have_row) {
                     // Neighbour fetch + visited test-and-insert.
                     if (!spilled && (int)(smem_count + rmax) > (H >> 1)) spilled = true;
                     uint32_t nb[kMaxRowPerLane];
@@ -839,6 +875,17 @@ const void *kernel_table(int nch, int rpl, int tw, bool staged) {
 #undef ROAR_KT
 #undef ROAR_KS
 #undef ROAR_K
+    return nullptr;
+}
+
+// Bipartite-graph kernels (FP32, one warp), instantiated by the FP32 unit.
+template <int DT>
+const void *kernel_table_bi_t(int nch, int rpl) {
+    static_assert(DT == 0, "bipartite search is FP32");
+#define ROAR_KB(N, R) \
+    if (nch == N && rpl == R) return (const void *)beam_search_kernel<DT, N, R, 1, 0, true>;
+    ROAR_KB(1, 2) ROAR_KB(1, 4) ROAR_KB(2, 2) ROAR_KB(2, 4) ROAR_KB(4, 2) ROAR_KB(4, 4) ROAR_KB(8, 2) ROAR_KB(8, 4)
+#undef ROAR_KB
     return nullptr;
 }
 

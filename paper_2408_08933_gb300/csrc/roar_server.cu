@@ -10,11 +10,15 @@
 // A host poller thread timestamps completions and relaunches the kernel when
 // work is pending but the kernel has exited (its teams exit after a bounded
 // idle period, so no launch can wait forever). Admission: a request is taken
-// only if the ring has room for all its queries; ring capacity comes from the
-// memory budget, each query charged its slot (query, results) and its search
-// state (pool of L_max entries).
+// only if the ring has room for all its queries and, under a memory budget,
+// if its charge fits beside the requests in flight. A query at (k, L) is
+// charged its ring bytes at its own k (query 4d, results 8k, counters 24),
+// its candidate pool (8L) and the exact visited table a beam of width L needs
+// (2^ceil(log2(32 L)) slots of 4 bytes, the kernel's own sizing rule for its
+// shared-memory table); a request gives its charge back when it is released.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -39,6 +43,7 @@ using Clock = std::chrono::steady_clock;
 struct Request {
     uint64_t first;   // sequence number of its first query
     int32_t nq, k;
+    int64_t charge = 0;   // bytes charged against the memory budget
     Clock::time_point t_submit, t_done;
     int32_t checked = 0;  // queries already seen done
     bool complete = false, released = false;
@@ -80,12 +85,22 @@ struct roar_server {
     uint64_t tail = 0;        // queries published
     uint64_t released = 0;    // queries whose slots are free again
     uint64_t completed_q = 0;
+    int64_t budget = 0;       // bytes of in-flight requests allowed (0: slots only)
+    int64_t inflight = 0;     // bytes charged to requests not yet released
     std::deque<Request> reqs; // submission order, trimmed when released
     std::atomic<bool> quit{false};
     std::thread poller;
 };
 
 namespace {
+
+// Bytes one query at (k, L) is charged: ring slot at its own k, candidate pool
+// and the exact visited table for a beam of width L.
+int64_t query_charge(int32_t d, int32_t k, int32_t L) {
+    int lg = 0;
+    while ((1ll << lg) < 32ll * L) ++lg;
+    return 4ll * d + 8ll * k + 24 + 8ll * L + (4ll << lg);
+}
 
 bool kernel_running(roar_server *s) {
     if (!s->launched) return false;
@@ -153,11 +168,13 @@ extern "C" roar_status roar_server_create(roar_index *idx, const roar_server_cfg
         return st;
     }
     s->d = a.d;
-    // Admission capacity: each in-flight query is charged its slot (query,
-    // results, counters) and the pool its search will need.
-    const int64_t per_query = (int64_t)s->d * 4 + (int64_t)s->k_max * 8 + 24 + (int64_t)s->L_max * 8;
+    // Ring capacity: given, or as many k_max-wide slots as the budget could
+    // hold; the budget itself is enforced per request at submission.
+    const int64_t slot_bytes = (int64_t)s->d * 4 + (int64_t)s->k_max * 8 + 24;
+    s->budget = cfg->memory_budget;
     s->R = cfg->ring_capacity ? cfg->ring_capacity
-                              : (cfg->memory_budget ? cfg->memory_budget / per_query : 65536);
+                              : (cfg->memory_budget ? std::min<int64_t>((int64_t)1 << 26, cfg->memory_budget / slot_bytes)
+                                                    : 65536);
     if (s->R < 1 || s->R > ((int64_t)1 << 26)) {
         set_error("roar_server_create: ring capacity must be 1..2^26 queries");
         delete s;
@@ -213,8 +230,19 @@ extern "C" roar_status roar_server_submit(roar_server *s, const float *q_host, i
         set_error("roar_server_submit: need 1 <= k <= k_max, k <= L <= L_max, nq >= 1");
         return ROAR_EINVAL;
     }
+    const int64_t charge = (int64_t)nq * query_charge(s->d, k, L);
+    if (s->budget > 0 && charge > s->budget) {
+        set_error("roar_server_submit: the request's charge exceeds the whole memory budget");
+        return ROAR_EINVAL;
+    }
+    if (nq > s->R) {
+        set_error("roar_server_submit: more queries than ring slots");
+        return ROAR_EINVAL;
+    }
     std::lock_guard<std::mutex> lock(s->mu);
-    if ((int64_t)(s->tail - s->released) + nq > s->R) return ROAR_EBUSY;  // admission
+    // Admission: free ring slots for every query, and room in the budget.
+    if ((int64_t)(s->tail - s->released) + nq > s->R) return ROAR_EBUSY;
+    if (s->budget > 0 && s->inflight + charge > s->budget) return ROAR_EBUSY;
     const uint64_t first = s->tail;
     for (int32_t i = 0; i < nq; ++i) {
         const size_t slot = (size_t)((first + (uint64_t)i) % (uint64_t)s->R);
@@ -230,6 +258,8 @@ extern "C" roar_status roar_server_submit(roar_server *s, const float *q_host, i
     r.first = first;
     r.nq = nq;
     r.k = k;
+    r.charge = charge;
+    s->inflight += charge;
     r.t_submit = Clock::now();
     s->reqs.push_back(r);
     *request_id = first;
@@ -263,6 +293,7 @@ extern "C" roar_status roar_server_poll(roar_server *s, uint64_t request_id, int
                 if (latency_s)
                     *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
                 r->released = true;
+                s->inflight -= r->charge;
                 // Slots free up in ring order.
                 while (!s->reqs.empty() && s->reqs.front().released) {
                     s->released = s->reqs.front().first + (uint64_t)s->reqs.front().nq;
@@ -287,6 +318,8 @@ extern "C" roar_status roar_server_stats(roar_server *s, double *out) {
     out[5] = (double)s->blocks;
     out[6] = (double)s->tw;
     out[7] = kernel_running(s) ? 1.0 : 0.0;
+    out[8] = (double)s->inflight;
+    out[9] = (double)s->budget;
     return ROAR_OK;
 }
 

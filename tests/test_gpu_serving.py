@@ -1,12 +1,14 @@
 """Serving loop: continuous batching into one persistent search kernel.
 
 Each query served in a mixed stream is bit-identical to searching it alone
-(the paper's beam search, Sec. 4.3, with its request's k and L)."""
+and to the oracle's beam search (Sec. 4.3) with its request's k and L;
+admission charges each request the memory its queries need."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2408_08933_gb300 as pkg
 import roarsynth as rs
 from gpu_util import dev_index, run
@@ -60,6 +62,10 @@ def test_mixed_stream_equals_alone(tiny, two_handles):
         alone = run(ref, q, k, L)
         assert np.array_equal(ids, alone[0]) and np.array_equal(dist, alone[1])
         assert np.array_equal(vis, alone[2]) and np.array_equal(st, alone[4])
+        o_ids, o_dist, o_vis, _, o_st = oracle.beam_search(tiny["X"], tiny["adj"], tiny["entry"], q, k, L,
+                                                           max_visits=MV)
+        assert np.array_equal(ids, o_ids) and np.array_equal(vis, o_vis) and np.array_equal(st, o_st)
+        assert np.allclose(dist, o_dist, rtol=1e-6, atol=0)
         assert lat > 0
     s = srv.stats()
     assert s["completed"] == s["submitted"] == qpos
@@ -70,7 +76,8 @@ def test_admission_refuses_when_ring_is_full(tiny, two_handles):
     serve, _ = two_handles
     srv = pkg.Server(serve, k_max=10, L_max=64, ring_capacity=64, idle_ms=20)
     Q = tiny["Q"]
-    assert srv.submit(Q[:65], 10, 32) is None          # larger than the ring
+    with pytest.raises(pkg.RoarError):
+        srv.submit(Q[:65], 10, 32)                      # more queries than the ring holds
     a = srv.submit(Q[:64], 10, 32)
     assert a is not None
     assert srv.submit(Q[:1], 10, 32) is None           # no room until released
@@ -112,4 +119,63 @@ def test_poll_timeout_is_bounded(tiny, two_handles):
     assert time.time() - t0 < 1.0
     if first is None:
         assert _drain(srv, {rid: (1000, 10)})
+    srv.close()
+
+
+def test_bf16_serving_matches_oracle(tiny):
+    """The serving form the benchmark runs: BF16 traversal + FP32 re-rank,
+    mixed (k, L) requests in flight together, each result the oracle's."""
+    X = tiny["X"]
+    codes = oracle.quant_bf16(X)
+    idx = dev_index(X, tiny["adj"], tiny["entry"], dtype="bf16", trav=codes.view(np.int16), max_visits=MV)
+    srv = pkg.Server(idx, k_max=100, L_max=400, ring_capacity=2048, idle_ms=20)
+    Q = tiny["Q"]
+    pending, meta = {}, {}
+    rng = np.random.default_rng(43)
+    for i in range(24):
+        nq = int(rng.integers(1, 30))
+        k = int(rng.choice([10, 100]))
+        L = int(rng.integers(max(k, 50), 401))
+        q = Q[(37 * i) % 900:(37 * i) % 900 + nq]
+        rid = srv.submit(q, k, L)
+        assert rid is not None
+        pending[rid] = (q.shape[0], k)
+        meta[rid] = (q, k, L)
+    for rid, (lat, ids, dist, vis, st) in _drain(srv, pending).items():
+        q, k, L = meta[rid]
+        o = oracle.beam_search(X, tiny["adj"], tiny["entry"], q, k, L, max_visits=MV, dtype="bf16", Xt=codes)
+        assert np.array_equal(ids, o[0]) and np.array_equal(vis, o[2]) and np.array_equal(st, o[4])
+        assert np.allclose(dist, o[1], rtol=1e-6, atol=0)
+    srv.close()
+    idx.close()
+
+
+def test_admission_by_memory(tiny, two_handles):
+    """Under a memory budget a request is admitted only if its charge (ring
+    slot at its k, pool 8L, exact visited table for width L, per query) fits
+    beside the requests in flight: with a small-L request in flight a large-L
+    one is refused while another small-L one is admitted; once released, the
+    large one fits. A request over the whole budget is an error."""
+    serve, ref = two_handles
+    d = tiny["X"].shape[1]
+    small, large = pkg.server_query_charge(d, 10, 50), pkg.server_query_charge(d, 10, 400)
+    assert large > 7 * small
+    budget = 8 * large
+    srv = pkg.Server(serve, k_max=100, L_max=400, memory_budget=budget, idle_ms=20)
+    Q = tiny["Q"]
+    a = srv.submit(Q[:8], 10, 50)
+    assert a is not None
+    assert srv.submit(Q[8:16], 10, 400) is None          # 8 small + 8 large > budget
+    c = srv.submit(Q[16:24], 10, 50)                      # 16 small fits
+    assert c is not None
+    assert srv.stats()["inflight_bytes"] == 16 * small
+    with pytest.raises(pkg.RoarError):
+        srv.submit(Q[:9], 10, 400)                        # 9 large > the whole budget
+    got = _drain(srv, {a: (8, 10), c: (8, 10)})
+    assert srv.stats()["inflight_bytes"] == 0
+    b = srv.submit(Q[8:16], 10, 400)
+    assert b is not None
+    got.update(_drain(srv, {b: (8, 10)}))
+    for rid, (q, L) in {a: (Q[:8], 50), c: (Q[16:24], 50), b: (Q[8:16], 400)}.items():
+        assert np.array_equal(got[rid][1], run(ref, q, 10, L)[0])
     srv.close()

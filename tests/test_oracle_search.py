@@ -142,3 +142,33 @@ def test_hand_traced_quantized_search_and_rerank():
             assert ids[0].tolist() == e[str(k)]["ids"], (name, k)
             assert dist[0].tolist() == e[str(k)]["dist"], (name, k)
             assert (int(visits[0]), int(hops[0]), int(st[0])) == (e["visits"], e["hops"], 0), name
+
+
+def test_hand_traced_bipartite_graph_search():
+    """G_bi (Alg. 1's bipartite step, every x -> t edge kept) and the greedy
+    search through query nodes (Sec. 4.1), traced by hand."""
+    g = load_golden("bipartite_search.json")
+    X, _ = path_graph(g["a"])
+    knn = np.array(g["knn"], np.uint32)
+    off, qids = oracle.bipartite(knn, X.shape[0])
+    assert off.tolist() == g["expect_off"] and qids.tolist() == g["expect_qids"]
+    q = np.array([[1, 0, 0, 0]], np.float32)
+    for c in g["cases"]:
+        ids, dist, visits, hops, st = oracle.beam_search_bi(X, knn, g["entry"], q, c["k"], c["L"], c["max_visits"])
+        assert ids[0].tolist() == c["ids"] and dist[0].tolist() == c["dist"], c["derivation"]
+        assert (int(visits[0]), int(hops[0]), int(st[0])) == (c["visits"], c["hops"], c["status"])
+
+
+def test_bipartite_search_complete_is_exact():
+    """One training query linked to every base row: expanding the entry scores
+    every row, so the result is the exact top-k under dot_fixed."""
+    rng = np.random.default_rng(23)
+    n, d = 50, 12
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    knn = np.array([[5] + [u for u in range(n) if u != 5]], np.uint32)
+    Q = rng.standard_normal((6, d)).astype(np.float32)
+    ids, dist, visits, hops, st = oracle.beam_search_bi(X, knn, 5, Q, 7, 7)
+    for i in range(len(Q)):
+        ref_ids, ref_d = _exact_topk_fixed(X, Q[i], 7)
+        assert ids[i].tolist() == ref_ids.tolist() and np.array_equal(dist[i], ref_d)
+    assert np.all(visits == n) and np.all(st == 0)
