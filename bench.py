@@ -57,7 +57,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -363,84 +363,164 @@ def _time_once(fn, torch, reps=3):
     return a.elapsed_time(b) / reps
 
 
+def _index_form(pkg, Xd, adj, entry, dtype):
+    """A search handle on (Xd, adj) traversing the given form's copy."""
+    if dtype == "f32":
+        return pkg.Index(Xd, adj, entry, max_visits=16384), None
+    codes, sc = pkg.quantize(Xd, dtype)
+    return pkg.Index(Xd, adj, entry, dtype=dtype, trav=codes, scales=sc, max_visits=16384), (codes, sc)
+
+
+def _free(torch):
+    import gc
+
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def _precision_section(torch, pkg, rs, w, log, steps=5, data=None):
+    """Precision form: FP32, BF16 and FP8-E4M3 (per-row scale) traversal copies
+    of one index, the last two re-ranked in FP32. Per form: the smallest L of
+    the sweep reaching recall@10 0.90, its QPS, the recall delta against FP32
+    at the same L, and per-result distance errors against FP64 on 200 sampled
+    queries (returned FP32 distances, and the traversal distances)."""
+    dev, X, Q, Xd, Qd, adj, entry, gt, bstats = data if data is not None else _setup(w, torch, pkg, rs, log)
+    nq = Q.shape[0]
+    sweepL = [50, 75, 100, 150, 200, 250, 300, 325, 350, 375, 400, 500]
+    sample = np.random.default_rng(1).choice(nq, 200, replace=False)
+    forms, sweeps = {}, {}
+    for dtype in ("f32", "bf16", "fp8"):
+        idx, keep = _index_form(pkg, Xd, adj, entry, dtype)
+        sw = _sweep(idx, Qd, gt, torch, sweepL)
+        sweeps[dtype] = sw
+        L, reached = _pick_L(sw)
+        idx.autotune(Qd, 10, L, repeats=1)
+        ms, out = _time_steps(idx, Qd, L, steps, 3, torch)
+        avg = sum(ms) / len(ms)
+        ids_h = out[0].cpu().numpy().view(np.uint32)
+        dh = out[1].cpu().numpy()[sample].astype(np.float64)
+        ih = ids_h[sample]
+        ref = -np.einsum("qkd,qd->qk", X[ih].astype(np.float64), Q[sample].astype(np.float64))
+        err = np.abs(dh - ref)
+        row = {"L": L, "recall_at_10": sw[L]["recall"], "recall_target_reached": reached,
+               "qps": nq / (avg / 1e3), "ms_per_step": avg, "visits": sw[L]["visits"],
+               "result_dist_err_vs_fp64": {"max": float(err.max()), "mean": float(err.mean())}}
+        if keep is not None:
+            codes, sc = keep
+            sel = torch.from_numpy(ih.ravel().astype(np.int64)).to(dev)
+            ch = codes[sel].cpu().numpy()
+            if dtype == "bf16":
+                dec = (ch.view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+            else:
+                dec = torch.from_numpy(ch).view(torch.float8_e4m3fn).double().numpy()
+                dec *= sc[sel].cpu().numpy().astype(np.float64)[:, None]
+            trav = -(dec.reshape(len(sample), 10, -1) * Q[sample].astype(np.float64)[:, None, :]).sum(-1)
+            terr = np.abs(trav - ref)
+            row["traversal_dist_err_vs_fp64"] = {"max": float(terr.max()), "mean": float(terr.mean())}
+        forms[dtype] = row
+        log(f"precision {dtype}: {row}")
+        idx.close()
+        del keep, out
+        _free(torch)
+    for dtype in ("bf16", "fp8"):
+        L = forms[dtype]["L"]
+        forms[dtype]["recall_delta_vs_f32_at_same_L"] = sweeps[dtype][L]["recall"] - sweeps["f32"][L]["recall"]
+    res = {"workload": f"{w.name}: base {w.n}x{w.d}, {w.n_train} training + {nq} test OOD queries, "
+                       f"{w.n_comp} components", "build": bstats, "forms": forms,
+           "sweep": {k: {str(L): v for L, v in sw.items()} for k, sw in sweeps.items()}}
+    del X, Q, Xd, Qd, adj, data
+    _free(torch)
+    return res
+
+
+def _uneven_section(torch, pkg, rs, w, dev, Xd, adj, entry, dtype, log):
+    """Uneven batch: 65,536 queries with k ~ U{1,10,100} and L ~ U[max(k,10),500]
+    in one persistent, CUDA-graph-captured launch (longest beams first)."""
+    idx, keep = _index_form(pkg, Xd, adj, entry, dtype)
+    nu = 65536
+    Qu = rs.test_queries(rs.scaled(w, n_test=nu))
+    ku, Lu = rs.uneven_params(nu, seed_tag=7)
+    Qud = torch.from_numpy(Qu).to(dev)
+    kud, Lud = torch.from_numpy(ku).to(dev), torch.from_numpy(Lu).to(dev)
+    uout = idx.uneven_outputs(ku)
+    best, _ = idx.autotune(Qud[:8192], 10, int(Lu.max()), repeats=1)   # the launch's pool-size bucket
+    plan = idx.plan_uneven(Qud, kud, Lud, int(Lu.max()), uout, longest_first=True)
+    for _ in range(2):
+        plan.launch()
+    torch.cuda.synchronize()
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_ev.record()
+    reps = 3
+    for _ in range(reps):
+        plan.launch()
+    b_ev.record()
+    torch.cuda.synchronize()
+    ums = a_ev.elapsed_time(b_ev) / reps
+    res = {"index": w.name, "base": f"{w.n}x{w.d}", "form": dtype if dtype == "f32" else f"{dtype} traversal + fp32 re-rank",
+           "queries": nu, "k": "U{1,10,100}", "L": "U[max(k,10),500]", "ms_per_launch": ums,
+           "qps": nu / (ums / 1e3), "graph_captured": True, "order": "longest L first",
+           "autotune_variant": int(best), "mean_visits": float(uout[3].double().mean()),
+           "status_nonzero": int((uout[5] != 0).sum())}
+    plan.close()
+    idx.close()
+    del Qud, uout, keep
+    _free(torch)
+    return res
+
+
+def _serving_section(torch, pkg, rs, w, dev, Xd, adj, entry, Q, Qd, gt, dtype, log):
+    """Continuous batching into the persistent kernel under an open-loop Poisson
+    stream (requests of 1..256 queries, k in {10, 100}, L in [50, 400]):
+    achieved QPS with p50/p99 latency per offered rate, and the recall of
+    served results for the test queries at the form's first L reaching 0.90."""
+    sidx, keep = _index_form(pkg, Xd, adj, entry, dtype)
+    sw = _sweep(sidx, Qd, gt, torch, [50, 75, 100, 150, 200, 300, 400])
+    L90, reached = _pick_L(sw)
+    sidx.autotune(Qd, 10, 400, repeats=1)
+    srv = pkg.Server(sidx, k_max=100, L_max=400, ring_capacity=1 << 16, idle_ms=50)
+    Qpool = rs.test_queries(rs.scaled(w, n_test=65536))
+    res = {"index": w.name, "base": f"{w.n}x{w.d}",
+           "form": dtype if dtype == "f32" else f"{dtype} traversal + fp32 re-rank",
+           "requests": "Poisson arrivals; 1..256 queries; k in {10,100}; L in [50,400]", "rates": []}
+    for j, rate in enumerate((1e4, 3e4, 1e5, 3e5, 1e6)):
+        res["rates"].append(_serve_rate(srv, Qpool, rate, 1.0, 200 + j))
+        log(f"serving {res['rates'][-1]}")
+    # served recall: the test queries in requests of 256 at L90
+    nq = Q.shape[0]
+    rids = []
+    for i in range(0, nq, 256):
+        rid = None
+        while rid is None:
+            rid = srv.submit(Q[i:i + 256], 10, L90)
+        rids.append((rid, min(256, nq - i)))
+    got = []
+    for rid, m in rids:
+        r = None
+        while r is None:
+            r = srv.poll(rid, m, 10, timeout_ms=100)
+        got.append(r[1])
+    res.update({"served_recall_at_10": _recall(np.concatenate(got), gt), "served_recall_L": L90,
+                "recall_target_reached": reached, "server": srv.stats()})
+    srv.close()
+    sidx.close()
+    del keep
+    _free(torch)
+    return res
+
+
 def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bstats, log):
     """The precision (10M x 512), uneven (1M x 512) and serving (10M x 200) workloads,
     and the OOD-built against ID-built graph comparison (ood)."""
     nq = Q.shape[0]
     res = {"mode": args.mode, "workload": w.name, "n": w.n, "d": w.d, "offset_norm": w.offset_norm, "build": bstats}
-    forms = {}
     if args.mode == "precision":
-        sweepL = [50, 75, 100, 150, 200, 300, 400, 500, 1024]
-        sample = np.random.default_rng(1).choice(nq, 200, replace=False)
-        for dtype in ("f32", "bf16", "fp8"):
-            if dtype == "f32":
-                idx = pkg.Index(Xd, adj, entry, max_visits=16384)
-                codes = sc = None
-            else:
-                codes, sc = pkg.quantize(Xd, dtype)
-                idx = pkg.Index(Xd, adj, entry, dtype=dtype, trav=codes, scales=sc, max_visits=16384)
-            rows = {}
-            for L in sweepL:
-                ms = _time_once(lambda: idx.search(Qd, 10, L), torch)
-                ids, dist, visits, hops, st = idx.search(Qd, 10, L)
-                torch.cuda.synchronize()
-                ids_h = ids.cpu().numpy().view(np.uint32)
-                rows[L] = {"qps": nq / (ms / 1e3), "recall_at_10": _recall(ids_h, gt),
-                           "visits": float(visits.double().mean()), "hops": float(hops.double().mean())}
-                if L == 500:
-                    # per-result distance error vs FP64, on 200 sampled queries
-                    dh = dist.cpu().numpy()[sample]
-                    ih = ids_h[sample]
-                    ref = -np.einsum("qkd,qd->qk", X[ih].astype(np.float64), Q[sample].astype(np.float64))
-                    err = np.abs(dh.astype(np.float64) - ref)
-                    rows[L]["result_dist_err_vs_fp64"] = {"max": float(err.max()), "mean": float(err.mean())}
-                    if codes is not None:
-                        sel = torch.from_numpy(ih.ravel().astype(np.int64)).to(dev)
-                        ch = codes[sel].cpu().numpy()
-                        if dtype == "bf16":
-                            dec = (ch.view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
-                        else:
-                            import torch as _t
-                            dec = _t.from_numpy(ch).view(_t.float8_e4m3fn).double().numpy()
-                            dec *= sc[sel].cpu().numpy().astype(np.float64)[:, None]
-                        trav = -(dec.reshape(len(sample), 10, -1) * Q[sample].astype(np.float64)[:, None, :]).sum(-1)
-                        terr = np.abs(trav - ref)
-                        rows[L]["traversal_dist_err_vs_fp64"] = {"max": float(terr.max()), "mean": float(terr.mean())}
-                log(f"{dtype} L={L}: {rows[L]}")
-            forms[dtype] = rows
-            idx.close()
-            del codes, sc
-        for dtype in ("bf16", "fp8"):
-            for L in sweepL:
-                forms[dtype][L]["recall_delta_vs_f32"] = forms[dtype][L]["recall_at_10"] - forms["f32"][L]["recall_at_10"]
-        res["forms"] = {k: {str(L): v for L, v in rows.items()} for k, rows in forms.items()}
+        res["precision"] = _precision_section(torch, pkg, rs, w, log,
+                                              data=(dev, X, Q, Xd, Qd, adj, entry, gt, bstats))
     elif args.mode == "uneven":
-        codes, sc = pkg.quantize(Xd, "bf16")
-        idx = pkg.Index(Xd, adj, entry, dtype="bf16", trav=codes, scales=None, max_visits=16384)
-        nu = 65536
-        Qu = rs.test_queries(rs.scaled(w, n_test=nu))
-        ku, Lu = rs.uneven_params(nu, seed_tag=7)
-        Qud, kud, Lud = (torch.from_numpy(a).to(dev) for a in (Qu, ku, Lu))
-        table = {}
-        for Lb in (32, 64, 128, 256, 512):
-            best, ms = idx.autotune(Qud[:8192], 10, Lb, repeats=1)
-            table[str(Lb)] = {"best_variant": int(best), "team_warps": [1, 2, 4, 8][best // 4],
-                              "ms": [round(float(x), 3) if x < 1e29 else None for x in ms]}
-        out = idx.uneven_outputs(ku)
-        plan = idx.plan_uneven(Qud, kud, Lud, int(Lu.max()), out, longest_first=True)
-        ms = _time_once(plan.launch, torch, reps=5)
-        offs = out[0].cpu().numpy()
-        mixed = out[1].cpu().numpy().view(np.uint32)
-        same = True
-        for i in np.random.default_rng(2).choice(nu, 64, replace=False):
-            ids, *_ = idx.search(Qud[i:i + 1], int(ku[i]), int(Lu[i]))
-            torch.cuda.synchronize()
-            same &= ids.cpu().numpy().view(np.uint32)[0].tolist() == mixed[offs[i]:offs[i] + ku[i]].tolist()
-        res.update({"queries": nu, "ms_per_launch": ms, "qps": nu / (ms / 1e3), "autotune": table,
-                    "alone_equals_mixed_on_64_samples": bool(same), "form": "bf16 traversal + fp32 re-rank",
-                    "graph_captured": True})
-        plan.close()
-        idx.close()
+        res["uneven"] = _uneven_section(torch, pkg, rs, w, dev, Xd, adj, entry, "bf16", log)
+    elif args.mode == "serving":
+        res["serving"] = _serving_section(torch, pkg, rs, w, dev, Xd, adj, entry, Q, Qd, gt, "bf16", log)
     elif args.mode == "ood":
         # The paper's central comparison on synthetic data: a graph built from
         # OOD training queries (RoarGraph as specified) against one built the
@@ -627,6 +707,9 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override base rows (smaller runs)")
     ap.add_argument("--n-train", type=int, default=0, help="override training queries")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="run the uneven batch and the serving loop on the main workload's index and skip "
+                         "the 10M x 512 precision workload")
     ap.add_argument("--n-comp", type=int, default=0, help="override the mixture components (small experiments)")
     ap.add_argument("--offset-norm", type=float, default=0.0,
                     help="override the OOD offset norm (ood mode experiments; the workloads use 1.5)")
@@ -710,10 +793,13 @@ def main():
     if dist_on:
         tdist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        torch.cuda.nvtx.range_push("timed_f32")
-        ms, out = _time_steps(idx, Qd, L, args.steps, args.warmup, torch)
-        torch.cuda.nvtx.range_pop()
+    # Clocks are sampled from before the warm-up until the end of the
+    # end-to-end loop (all of it GPU-busy), so the timed region is inside.
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.5)                      # nvidia-smi takes a moment to start sampling
+    torch.cuda.nvtx.range_push("timed_f32")
+    ms, out = _time_steps(idx, Qd, L, args.steps, args.warmup, torch)
+    torch.cuda.nvtx.range_pop()
     if dist_on:
         tdist.barrier()
     total_ms = max_over_ranks(sum(ms), dev if dist_on else None)
@@ -745,6 +831,7 @@ def main():
     for _ in range(args.steps):
         idx.search_host(Qh, 10, L, out=hout)
     e2e_s = time.perf_counter() - t0
+    clk.__exit__(None, None, None)
     h_ids = hout[0].numpy().view(np.uint32)
     assert np.array_equal(h_ids, ids.cpu().numpy().view(np.uint32)), "host-buffer results differ"
 
@@ -772,49 +859,29 @@ def main():
         forms["f32"] = {"L": L, "recall_at_10": sweep[L]["recall"], "qps": value / world,
                         "ms_per_step": avg_ms, "achieved_gbs": achieved}
 
-    # ---- uneven batch: per-query k and L in one graph-captured persistent launch ----
-    uneven = None
+    # ---- the other workloads the metric names ----------------------------------
+    # precision form: 10M x 512 (FP32 / BF16 / FP8 + re-rank); uneven batch:
+    # 1M x 512 BF16 + re-rank; serving: 10M x 200 BF16 + re-rank. With --quick
+    # the uneven batch and the serving loop run on this workload's index.
+    precision = uneven = serving = None
     if not args.no_forms:
-        nu = 65536
-        Qu = rs.test_queries(rs.scaled(w, n_test=nu))
-        ku, Lu = rs.uneven_params(nu, seed_tag=7)
-        Qud = torch.from_numpy(Qu).to(dev)
-        kud, Lud = torch.from_numpy(ku).to(dev), torch.from_numpy(Lu).to(dev)
-        uout = idx.uneven_outputs(ku)
-        idx.autotune(Qud[:8192], 10, int(Lu.max()), repeats=1)   # the launch's pool-size bucket
-        plan = idx.plan_uneven(Qud, kud, Lud, int(Lu.max()), uout, longest_first=True)
-        for _ in range(2):
-            plan.launch()
-        torch.cuda.synchronize()
-        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a_ev.record()
-        reps = 3
-        for _ in range(reps):
-            plan.launch()
-        b_ev.record()
-        torch.cuda.synchronize()
-        ums = a_ev.elapsed_time(b_ev) / reps
-        uneven = {"queries": nu, "k": "U{1,10,100}", "L": "U[max(k,10),500]", "ms_per_launch": ums,
-                  "qps": nu / (ums / 1e3), "graph_captured": True, "order": "longest L first",
-                  "mean_visits": float(uout[3].double().mean()), "status_nonzero": int((uout[5] != 0).sum())}
-        plan.close()
-        del Qud, uout
-
-    # ---- serving: continuous batching into the persistent kernel ------------------
-    serving = None
-    if not args.no_forms:
-        sidx = pkg.Index(Xd, adj, entry, max_visits=16384)
-        sidx.autotune(Qd, 10, 400, repeats=1)
-        srv = pkg.Server(sidx, k_max=100, L_max=400, ring_capacity=1 << 16, idle_ms=50)
-        Qpool = rs.test_queries(rs.scaled(w, n_test=65536))
-        serving = {"index": w.name, "requests": "Poisson arrivals; 1..256 queries; k in {10,100}; "
-                                              "L in [50,400]", "rates": []}
-        for j, rate in enumerate((1e4, 3e4, 1e5, 3e5, 1e6)):
-            serving["rates"].append(_serve_rate(srv, Qpool, rate, 1.0, 200 + j))
-            log(f"serving {serving['rates'][-1]}")
-        serving["server"] = srv.stats()
-        srv.close()
-        sidx.close()
+        if args.quick:
+            uneven = _uneven_section(torch, pkg, rs, w, dev, Xd, adj, entry, "bf16", log)
+            serving = _serving_section(torch, pkg, rs, w, dev, Xd, adj, entry, Q, Qd, gt, "bf16", log)
+        else:
+            wu = rs.BASE_1M_D512
+            du = _setup(wu, torch, pkg, rs, log)
+            uneven = _uneven_section(torch, pkg, rs, wu, du[0], du[3], du[5], du[6], "bf16", log)
+            del du
+            _free(torch)
+            ws = rs.BASE_10M_D200
+            ds = _setup(ws, torch, pkg, rs, log)
+            serving = _serving_section(torch, pkg, rs, ws, ds[0], ds[3], ds[5], ds[6], ds[2], ds[4], ds[7],
+                                       "bf16", log)
+            serving["build"] = ds[8]
+            del ds
+            _free(torch)
+            precision = _precision_section(torch, pkg, rs, rs.BASE_10M_D512, log)
 
     cpu = parity = gt_check = None
     if rank == 0:
@@ -840,6 +907,7 @@ def main():
         "ground_truth_check": gt_check,
         "clocks": clk.summary(),
         "forms": forms,
+        "precision": precision,
         "uneven": uneven,
         "serving": serving,
         "sweep": {str(k): v for k, v in sweep.items()},
