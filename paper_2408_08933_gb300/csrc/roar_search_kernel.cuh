@@ -164,12 +164,18 @@ __device__ __forceinline__ float4 to_f4(const RawChunk<DT> &r) {
 #endif
 // The FP32 re-rank inside the BF16 / FP8 kernels gathers fewer rows per batch
 // (ROAR_RERANK_CHUNKS loads per lane): those kernels run with fewer registers.
+// With wide rows (ROAR_RERANK_CHUNKS_WIDE; on GB300 at 1M x 512, 8 chunks,
+// i.e. 2 rows per batch, beat 16 by 3-10 %: the wider batch spilled).
 #ifndef ROAR_RERANK_CHUNKS
 #define ROAR_RERANK_CHUNKS 8
 #endif
+#ifndef ROAR_RERANK_CHUNKS_WIDE
+#define ROAR_RERANK_CHUNKS_WIDE 8
+#endif
 template <int NCH>
 __host__ __device__ constexpr int rerank_rows() {
-    return NCH >= ROAR_RERANK_CHUNKS ? 1 : ROAR_RERANK_CHUNKS / NCH;
+    return NCH >= 4 ? (NCH >= ROAR_RERANK_CHUNKS_WIDE ? 1 : ROAR_RERANK_CHUNKS_WIDE / NCH)
+                    : (NCH >= ROAR_RERANK_CHUNKS ? 1 : ROAR_RERANK_CHUNKS / NCH);
 }
 template <int DT, int NCH>
 __host__ __device__ constexpr int batch_rows() {
@@ -219,14 +225,26 @@ __device__ __forceinline__ float reduce_rows(const float (&s)[B], int lane) {
 // Distances for rows ids_s[j] (shared, expanded bit ignored), j = first,
 // first + 1, ... in groups of B, groups `step` apart (one warp's share of a
 // team); writes -<q, x> (times the row scale for FP8) to out_s[j].
+// ahead > 0: while scoring a batch, ask L2 for this warp's batch `ahead`
+// batches later (and for the first `ahead` batches up front).
 template <int DT, int NCH, int B>
 __device__ __forceinline__ void score_rows(const void *base, const float *scales, int d, int d4,
                                            const float4 (&qr)[NCH], const uint32_t *ids_s, int cnt,
-                                           float *out_s, int lane, int first = 0, int step = B) {
+                                           float *out_s, int lane, int first = 0, int step = B, int ahead = 0) {
     constexpr int RS = reduce_stride<B>();
+    const uint32_t rowbytes = (uint32_t)d * (4u >> DT);
+    if (ROAR_PREFETCH_ROWS)
+        for (int a = 0; a < ahead; ++a) {
+            const int p0 = first + a * step;
+            if (p0 < cnt) prefetch_rows_l2(base, rowbytes, ids_s + p0, min(B, cnt - p0), lane);
+        }
     const int rr = lane / RS;                          // the row this lane sums and writes
     const bool writer = (lane & (RS - 1)) == 0 && rr < B;
     for (int j0 = first; j0 < cnt; j0 += step) {
+        if (ROAR_PREFETCH_ROWS && ahead > 0) {
+            const int p0 = j0 + ahead * step;
+            if (p0 < cnt) prefetch_rows_l2(base, rowbytes, ids_s + p0, min(B, cnt - p0), lane);
+        }
         RawChunk<DT> raw[B][NCH];
         float sc = 1.0f;  // FP8: the writer of row j0 + rr holds its scale, loaded with the rows
         if constexpr (DT == 2) {
@@ -452,13 +470,13 @@ __device__ __forceinline__ int lower_bound_entries(const float *dv, const uint32
 
 
 // Launch shape of a team of TW warps per query: CTAs of max(4, TW) warps,
-// with the register budget of min_blocks_per_sm<DT>() 4-warp CTAs per SM.
-template <int DT, int TW, int STG = 0>
+// with the register budget of min_blocks_per_sm<DT, NCH>() 4-warp CTAs per SM.
+template <int DT, int TW, int STG = 0, int NCH = 1>
 struct TeamShape {
     static constexpr int kThreads = 32 * (TW > kWarpsPerBlock ? TW : kWarpsPerBlock);
     static constexpr int kTeams = kThreads / (32 * TW);
     static constexpr int kWarpBudget =
-        (STG > 0 && DT == 0 ? ROAR_MIN_BLOCKS_STAGED : min_blocks_per_sm<DT>()) * kWarpsPerBlock;
+        (STG > 0 && DT == 0 ? ROAR_MIN_BLOCKS_STAGED : min_blocks_per_sm<DT, NCH>()) * kWarpsPerBlock;
     static constexpr int kMinBlocks = (kWarpBudget * 32) / kThreads > 0 ? (kWarpBudget * 32) / kThreads : 1;
 };
 
@@ -477,7 +495,7 @@ struct TeamShape {
 // merging all of v's two-hop neighbours at once. The visit cap is checked
 // before each query node's row.
 template <int DT, int NCH, int RPL, int TW, int STG, bool BI = false>
-__global__ void __launch_bounds__(TeamShape<DT, TW, STG>::kThreads, TeamShape<DT, TW, STG>::kMinBlocks)
+__global__ void __launch_bounds__(TeamShape<DT, TW, STG, NCH>::kThreads, TeamShape<DT, TW, STG, NCH>::kMinBlocks)
 beam_search_kernel(const SearchArgs a) {
     static_assert(!BI || (DT == 0 && TW == 1 && STG == 0), "bipartite search: FP32, one warp, register gather");
     constexpr int kMaxRowPerLane = RPL;
@@ -863,8 +881,10 @@ beam_search_kernel(const SearchArgs a) {
         const int fsize = ctl[2];
         auto deleted = [&](uint32_t u) -> bool { return (__ldcg(a.tomb + (u >> 5)) >> (u & 31)) & 1u; };
         if constexpr (DT != 0) {
-            if (ROAR_PREFETCH_ROWS && leader) prefetch_rows_l2(a.base32, (uint32_t)d * 4u, pi, fsize, lane);
-            score_rows<0, NCH, B0>(a.base32, nullptr, d, d4, qr, pi, fsize, pd, lane, wt * B0, TW * B0);
+            // The pool's FP32 rows are asked of L2 a few batches ahead (all at
+            // once would be evicted before use for long pools).
+            score_rows<0, NCH, B0>(a.base32, nullptr, d, d4, qr, pi, fsize, pd, lane, wt * B0, TW * B0,
+                                   (16 + B0 - 1) / B0);
             tsync();
             if (leader) {
                 int alive = fsize;
