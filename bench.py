@@ -844,7 +844,9 @@ def main():
             qs = _sweep(qidx, Qd, gt, torch, L_SWEEP)
             qL, _ = _pick_L(qs)
             qidx.autotune(Qd, 10, qL, repeats=2)
+            torch.cuda.nvtx.range_push(f"timed_{dtype}")
             qms, qout = _time_steps(qidx, Qd, qL, max(3, args.steps // 2), 3, torch)
+            torch.cuda.nvtx.range_pop()
             qv = float(qout[2].double().mean())
             qh = float(qout[3].double().mean())
             qbytes = _algorithmic_bytes(qv, qh, deg_mean, w.d, eb, sb, k_rerank_L=qL)
