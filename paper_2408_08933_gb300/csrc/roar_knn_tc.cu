@@ -21,7 +21,11 @@
 // Every mbarrier wait is bounded (wait_ns of wall time per wait): on timeout
 // the kernel sets *err, waits for its own copies and for the MMAs it has
 // issued, frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <cstdlib>
+#include <cstring>
 
 #include "roar_internal.cuh"
 
@@ -60,6 +64,32 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// The same for the 128-byte-swizzled K-major layout TMA writes: rows of 128
+// bytes (64 BF16 of K), the 16-byte pieces of row r at piece ^ (r % 8),
+// 8-row atoms 1024 bytes apart (stride offset); the atoms are 1024-byte
+// aligned (base offset 0). A K step of 16 elements advances the start by 32
+// bytes inside the atom. Swizzle mode 2 (128-byte) in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    return smem_desc(saddr, 16, 1024) | ((uint64_t)2 << 61);
+}
+
+// Arm a barrier for `bytes` of asynchronous copies (one arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: the box at (x = column, y = row) of the 2-D tensor map to shared
+// memory; completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -284,11 +314,16 @@ __device__ __forceinline__ void stage_chunk(uint32_t dst, const __nv_bfloat16 *s
 // barriers), 2 issues the MMAs (lane 0; stage freed through "empty" barriers
 // by tcgen05.commit) and owns TMEM, 3-6 read the two alternating 256-column
 // accumulators (rows 32 * (warp % 4) + lane) while the next tile is computed.
+// kTma: operands staged by TMA (one thread issues 2-D tensor-map copies into
+// the 128-byte-swizzled layout, completion counted in bytes on the "full"
+// barriers) instead of the two cp.async producer warps and the no-swizzle
+// layout.
+template <bool kTma>
 __global__ void __launch_bounds__(kThreads, 1)
 knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat16 *__restrict__ X,
               int64_t n, int d, int stages, int C, float *__restrict__ buf_s,
               uint32_t *__restrict__ buf_i, uint32_t *__restrict__ out_i, int *__restrict__ err,
-              uint64_t wait_ns) {
+              uint64_t wait_ns, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], acc_full[2], acc_empty[2], a_full, drain_bar;
     __shared__ uint32_t tmem_slot;
@@ -297,7 +332,8 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nkc = (d + kKC - 1) / kKC;
-    const uint32_t a_base = smem_addr(smem);
+    // TMA's 128-byte swizzle repeats every 1024 bytes: start the operands there.
+    const uint32_t a_base = kTma ? ((smem_addr(smem) + 1023u) & ~1023u) : smem_addr(smem);
     const uint32_t b_base = a_base + (uint32_t)nkc * kChunkA;
     const int64_t m0 = (int64_t)blockIdx.x * kTM;
     const int64_t ntiles = (n + kTN - 1) / kTN;
@@ -305,14 +341,14 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
 
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full_bar[s], kProducers);
+            mbar_init(&full_bar[s], kTma ? 1 : kProducers);
             mbar_init(&empty_bar[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 4 * 32);
         }
-        mbar_init(&a_full, kProducers);
+        mbar_init(&a_full, kTma ? 1 : kProducers);
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -327,7 +363,33 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp < 2) {
+    if (kTma && warp < 2) {
+        // ---- producer: one thread issues every TMA copy ----
+        if (warp == 0 && lane == 0) {
+            int64_t last_g[kMaxStages];
+            for (int s = 0; s < kMaxStages; ++s) last_g[s] = -1;
+            mbar_expect_tx(&a_full, (uint32_t)nkc * kChunkA);
+            for (int c = 0; c < nkc; ++c) tma_load_2d(a_base + (uint32_t)c * kChunkA, &tmA, c * kKC, (int32_t)m0, &a_full);
+            for (int64_t g = 0; g < nchunks; ++g) {
+                const int s = (int)(g % stages);
+                const uint32_t use = (uint32_t)(g / stages);
+                if (use > 0 && !mbar_wait(&empty_bar[s], (use - 1) & 1, abort_v, wait_ns)) break;
+                const int64_t t = g / nkc;
+                const int c = (int)(g - t * nkc);
+                mbar_expect_tx(&full_bar[s], kChunkB);
+                tma_load_2d(b_base + (uint32_t)s * kChunkB, &tmB, c * kKC, (int32_t)(t * kTN), &full_bar[s]);
+                last_g[s] = g;
+            }
+            // No copy may still be landing when the CTA exits (after an abort
+            // some armed stages are never consumed): wait, bounded, for the
+            // last phase armed on every barrier.
+            bool drained = mbar_drain(&a_full, 0);
+            for (int s = 0; s < stages; ++s)
+                if (last_g[s] >= 0) drained = mbar_drain(&full_bar[s], (uint32_t)(last_g[s] / stages) & 1) && drained;
+            if (!drained) *abort_v = 1;
+        }
+        __syncwarp();
+    } else if (warp < 2) {
         // ---- producers ----
         for (int c = 0; c < nkc; ++c) stage_chunk(a_base + (uint32_t)c * kChunkA, T, m0, kTM, nt, d, c * kKC, tid, kProducers);
         cp_async_arrive(&a_full);
@@ -346,7 +408,7 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
         if (lane == 0) {
             bool issued = false;
             if (mbar_wait(&a_full, 0, abort_v, wait_ns)) {
-                fence_async_smem();  // cp.async data, written through the generic proxy, to the tensor core
+                if (!kTma) fence_async_smem();  // cp.async data, written through the generic proxy, to the tensor core
                 int64_t g = 0;
                 bool ok = true;
                 for (int64_t t = 0; t < ntiles && ok; ++t) {
@@ -360,14 +422,14 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
                             ok = false;
                             break;
                         }
-                        fence_async_smem();
+                        if (!kTma) fence_async_smem();
                         tc_fence_after();
                         const uint32_t a_chunk = a_base + (uint32_t)c * kChunkA;
                         const uint32_t b_chunk = b_base + (uint32_t)s * kChunkB;
 #pragma unroll
                         for (int ks = 0; ks < kKC / 16; ++ks) {
-                            const uint64_t ad = smem_desc(a_chunk + ks * 256, 128, 1024);
-                            const uint64_t bd = smem_desc(b_chunk + ks * 256, 128, 1024);
+                            const uint64_t ad = kTma ? smem_desc_sw128(a_chunk + ks * 32) : smem_desc(a_chunk + ks * 256, 128, 1024);
+                            const uint64_t bd = kTma ? smem_desc_sw128(b_chunk + ks * 32) : smem_desc(b_chunk + ks * 256, 128, 1024);
                             tc_mma(tmem + (uint32_t)(b * kTN), ad, bd, (c > 0 || ks > 0) ? 1u : 0u);
                         }
                         issued = true;
@@ -502,6 +564,56 @@ size_t knn_tc_smem_bytes(int d) {
     return need < 120 * 1024 ? 120 * 1024 : need;  // one CTA per SM: it holds all 512 TMEM columns
 }
 
+namespace {
+
+// cuTensorMapEncodeTiled, looked up through the runtime (no link to the
+// driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// A BF16 matrix [rows][d] (row-major, d % 8 == 0 so rows are 16-byte multiples)
+// read in boxes of 64 columns x box_rows rows with the 128-byte swizzle; reads
+// past the last row or column return zeros.
+bool make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int d, int box_rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)d * 2u};
+    const cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// Operand staging of the kNN kernel: TMA (1) or the cp.async producer warps
+// (0). ROAR_KNN_TMA in the environment overrides the default.
+#ifndef ROAR_KNN_TMA_DEFAULT
+#define ROAR_KNN_TMA_DEFAULT 1
+#endif
+static bool knn_use_tma() {
+    static const bool use = []() {
+        const char *e = std::getenv("ROAR_KNN_TMA");
+        return e ? std::atoi(e) != 0 : ROAR_KNN_TMA_DEFAULT != 0;
+    }();
+    return use;
+}
+
 // Candidates (best C per row, unsorted, 0xFFFFFFFF padded) of nt rows of T16
 // against X16 into cand [nt][C]; buf_s/buf_i are [nt][cap] scratch.
 cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloat16 *X16, int64_t n, int d,
@@ -511,11 +623,23 @@ cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloa
     // A cut must leave room for a whole tile: C + kTN <= kCap.
     if (stages < 2 || cap != kCap || C < 1 || C + kTN > kCap) return cudaErrorInvalidValue;
     const size_t smem = knn_tc_smem_bytes(d);
-    cudaError_t e = cudaFuncSetAttribute(knn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int64_t blocks = (nt + kTM - 1) / kTM;
-    knn_tc_kernel<<<(unsigned)blocks, kThreads, smem, s>>>(T16, nt, X16, n, d, stages, C, buf_s, buf_i,
-                                                           cand, err, wait_ns);
+    alignas(64) CUtensorMap tmA, tmB;
+    std::memset(&tmA, 0, sizeof tmA);
+    std::memset(&tmB, 0, sizeof tmB);
+    const bool tma = knn_use_tma() && (d % 8) == 0 && make_map(&tmA, T16, nt, d, kTM) && make_map(&tmB, X16, n, d, kTN);
+    cudaError_t e;
+    if (tma) {
+        e = cudaFuncSetAttribute(knn_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_tc_kernel<true><<<(unsigned)blocks, kThreads, smem, s>>>(T16, nt, X16, n, d, stages, C, buf_s, buf_i,
+                                                                     cand, err, wait_ns, tmA, tmB);
+    } else {
+        e = cudaFuncSetAttribute(knn_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_tc_kernel<false><<<(unsigned)blocks, kThreads, smem, s>>>(T16, nt, X16, n, d, stages, C, buf_s, buf_i,
+                                                                      cand, err, wait_ns, tmA, tmB);
+    }
     return cudaGetLastError();
 }
 
