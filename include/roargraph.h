@@ -100,6 +100,29 @@ roar_status roar_index_create(int64_t n, int32_t d, const float *base_f32, roar_
                               int32_t rmax, uint32_t entry, uint32_t max_visits, roar_index **out);
 
 /*
+ * RoarGraph construction in the literal order of Alg. 1 (Sec. 4.2), composed
+ * of the library's GPU parts, for checking them against the paper's steps on
+ * small inputs (roar_build_index is the batched, fast form; see DESIGN):
+ * training-query kNN (roar_knn, GPU); bipartite step; projection (Alg. 2)
+ * with pivots in ascending id and every reverse edge applied before the next
+ * pivot (host); connectivity enhancement with every base row searched over
+ * the fixed G_pj (roar_search, GPU, width L_build) and its list pruned with
+ * Alg. 3 without fill (roar_acquire, GPU), then the lists and reverse edges
+ * applied in ascending row order (host); the final union; and the repair
+ * (each unreachable node, smallest id first, gets an edge from its nearest
+ * reachable node with a free slot, else the nearest gives up its last edge).
+ * Every decision uses the search's fixed-order FP32 distance, ties by id.
+ *   Arguments as roar_build_index (no thread count: the sequential steps run
+ *   on one host thread; n <= 2^24, d % 8 == 0, d <= 512).
+ *   stats [16]: [0] seconds, [6] pivots, [7] G_pj edges, [8] final edges,
+ *   [9] nodes unreachable before the repair, [10] repairs.
+ * Synchronises `stream`. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ */
+roar_status roar_build_index_literal(const float *X_dev, int64_t n, int32_t d, const float *T_dev, int64_t nt,
+                                     int32_t nq_depth, int32_t M, int32_t L_build, uint32_t *adj_dev,
+                                     uint32_t *pj_dev, uint32_t *entry_out, double *stats, void *stream);
+
+/*
  * The query-base bipartite graph G_bi of Alg. 1 (Sec. 4.2.2) from the
  * training queries' kNN lists: query node t has out-edges to its N_q - 1
  * nearest base rows after the first (N_out(t)); the nearest, x, gets the

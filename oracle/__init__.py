@@ -108,6 +108,8 @@ def _load():
         lib.orc_repair.restype = i64
         lib.orc_build.argtypes = [P, i64, i64, i32, P, i32, i32, i32, u32, P, P, P]
         lib.orc_build.restype = ctypes.c_int
+        lib.orc_build_prec.argtypes = [P, i64, i64, i32, P, i32, i32, i32, u32, P, P, P, i32]
+        lib.orc_build_prec.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -247,9 +249,12 @@ def repair(X, adj, entry: int):
     return adj, int(r), int(u0[0])
 
 
-def build_index(X, knn_ids, M: int, L: int, entry: int):
+def build_index(X, knn_ids, M: int, L: int, entry: int, precision: str = "f64"):
     """Alg. 1: bipartite graph, projection (Alg. 2), connectivity enhancement,
-    then reachability repair. Returns (final adj [n][2M], G_pj [n][M], stats)."""
+    then reachability repair. Returns (final adj [n][2M], G_pj [n][M], stats).
+    precision "f64": every construction distance in FP64; "f32": the search's
+    fixed-order FP32 dot (the precision a GPU construction decides in), same
+    steps."""
     X = _f32(X)
     knn_ids = np.ascontiguousarray(knn_ids, dtype=np.uint32)
     n, d = X.shape
@@ -257,8 +262,9 @@ def build_index(X, knn_ids, M: int, L: int, entry: int):
     adj = np.empty((n, 2 * M), dtype=np.uint32)
     pj = np.empty((n, M), dtype=np.uint32)
     stats = np.zeros(8, dtype=np.int64)
-    rc = _load().orc_build(_p(X), n, nt, d, _p(knn_ids), nqd, M, L, entry, _p(pj), _p(adj),
-                           _p(stats))
+    prec = {"f64": 0, "f32": 1}[precision]
+    rc = _load().orc_build_prec(_p(X), n, nt, d, _p(knn_ids), nqd, M, L, entry, _p(pj), _p(adj),
+                                _p(stats), prec)
     if rc != 0:
         raise RuntimeError(f"orc_build failed: {rc}")
     keys = ["pivots", "proj_reprunes", "ce_reprunes", "repairs", "pj_edges", "final_edges",

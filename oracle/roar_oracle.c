@@ -84,6 +84,14 @@ static double dist64(const float *a, const float *b, int32_t d) {
 
 double orc_dist_f64(const float *a, const float *b, int32_t d) { return dist64(a, b, d); }
 
+/* Construction distances: FP64 in index order (prec 0, the construction's
+ * default here) or -dot_fixed, the search's fixed-order FP32 dot (prec 1),
+ * the precision a GPU construction takes its decisions in; held in a double
+ * either way (FP32 -> FP64 is exact, so the orders agree). */
+static double cdist(int prec, const float *a, const float *b, int32_t d) {
+    return prec ? -(double)orc_dot_fixed(a, b, d) : dist64(a, b, d);
+}
+
 static int less_f32(float da, uint32_t ia, float db, uint32_t ib) {
     return da < db || (da == db && ia < ib);
 }
@@ -592,7 +600,7 @@ static int cmp_ent64(const void *a, const void *b) {
  * With fill, the remaining candidates are appended in order until |Res| = M.
  * Returns |Res| written to res (capacity M).
  */
-static int32_t acquire_neighbors(const float *X, int32_t d, uint32_t x, const ent64 *C, int32_t nc,
+static int32_t acquire_neighbors(int prec, const float *X, int32_t d, uint32_t x, const ent64 *C, int32_t nc,
                                  int32_t M, int fill, uint32_t *res) {
     int32_t nr = 0;
     const float *xv = X + (int64_t)x * d;
@@ -604,10 +612,10 @@ static int32_t acquire_neighbors(const float *X, int32_t d, uint32_t x, const en
             if (res[j] == c) dup = 1;
         if (dup) continue;
         if (nr == 0) { res[nr++] = c; continue; }            /* the closest candidate */
-        double dxc = dist64(xv, X + (int64_t)c * d, d);
+        double dxc = cdist(prec, xv, X + (int64_t)c * d, d);
         int keep = 1;
         for (int32_t j = 0; j < nr && keep; ++j)
-            if (!(dxc < dist64(X + (int64_t)c * d, X + (int64_t)res[j] * d, d))) keep = 0;
+            if (!(dxc < cdist(prec, X + (int64_t)c * d, X + (int64_t)res[j] * d, d))) keep = 0;
         if (keep) res[nr++] = c;
     }
     if (fill) {
@@ -635,7 +643,7 @@ int32_t orc_acquire_neighbors(const float *X, int64_t n, int32_t d, uint32_t x, 
         C[i].id = cand[i];
         C[i].d = dist64(X + (int64_t)x * d, X + (int64_t)cand[i] * d, d);
     }
-    int32_t r = acquire_neighbors(X, d, x, C, nc, M, fill, res);
+    int32_t r = acquire_neighbors(0, X, d, x, C, nc, M, fill, res);
     free(C);
     return r;
 }
@@ -683,7 +691,7 @@ int32_t orc_acquire_neighbors_f32(const float *X, int64_t n, int32_t d, uint32_t
 /* Reverse-edge update of Alg. 2 and of Alg. 1's enhancement loop: give p the edge
  * p -> x. Skip when present; append when there is room; otherwise re-prune
  * N(p) U {x} with Alg. 3. */
-static int reverse_update(const float *X, int32_t d, ulist *G, uint32_t p, uint32_t x, int32_t M,
+static int reverse_update(int prec, const float *X, int32_t d, ulist *G, uint32_t p, uint32_t x, int32_t M,
                           int fill, ent64 *buf, uint32_t *res, int64_t *reprunes) {
     ulist *lp = &G[p];
     if (ul_has(lp, x)) return ORC_OK;
@@ -692,14 +700,14 @@ static int reverse_update(const float *X, int32_t d, ulist *G, uint32_t p, uint3
     int32_t nc = 0;
     for (int32_t i = 0; i < lp->n; ++i) {
         buf[nc].id = lp->v[i];
-        buf[nc].d = dist64(pv, X + (int64_t)lp->v[i] * d, d);
+        buf[nc].d = cdist(prec, pv, X + (int64_t)lp->v[i] * d, d);
         ++nc;
     }
     buf[nc].id = x;
-    buf[nc].d = dist64(pv, X + (int64_t)x * d, d);
+    buf[nc].d = cdist(prec, pv, X + (int64_t)x * d, d);
     ++nc;
     qsort(buf, (size_t)nc, sizeof(ent64), cmp_ent64);
-    int32_t nr = acquire_neighbors(X, d, p, buf, nc, M, fill, res);
+    int32_t nr = acquire_neighbors(prec, X, d, p, buf, nc, M, fill, res);
     lp->n = 0;
     for (int32_t i = 0; i < nr; ++i)
         if (ul_push(lp, res[i])) return ORC_ENOMEM;
@@ -710,13 +718,13 @@ static int reverse_update(const float *X, int32_t d, ulist *G, uint32_t p, uint3
 /* FP64 beam search over adjacency lists G (used by connectivity enhancement,
  * the enhancement loop of Alg. 1). Same algorithm as search_one with FP64 distances and no
  * visit cap. Writes the final pool (sorted, size returned). */
-static int32_t beam_search_f64_lists(const float *X, int64_t n, int32_t d, const ulist *G,
+static int32_t beam_search_f64_lists(int prec, const float *X, int64_t n, int32_t d, const ulist *G,
                                      uint32_t entry, const float *q, int32_t L, ent64 *pool,
                                      unsigned char *checked, unsigned char *visited) {
     int32_t size = 0;
     memset(visited, 0, (size_t)n);
     visited[entry] = 1;
-    pool[0].d = dist64(q, X + (int64_t)entry * d, d);
+    pool[0].d = cdist(prec, q, X + (int64_t)entry * d, d);
     pool[0].id = entry;
     checked[0] = 0;
     size = 1;
@@ -731,7 +739,7 @@ static int32_t beam_search_f64_lists(const float *X, int64_t n, int32_t d, const
             uint32_t u = G[v].v[j];
             if (visited[u]) continue;
             visited[u] = 1;
-            double dd = dist64(q, X + (int64_t)u * d, d);
+            double dd = cdist(prec, q, X + (int64_t)u * d, d);
             int32_t pos;
             if (size == L) {
                 if (!less_f64(dd, u, pool[L - 1].d, pool[L - 1].id)) continue;
@@ -768,8 +776,8 @@ static int32_t beam_search_f64_lists(const float *X, int64_t n, int32_t d, const
  * Returns the number of repairs (-1 when out of memory); *unreachable0 gets
  * the number of nodes unreachable before the first repair.
  */
-int64_t orc_repair(const float *X, int64_t n, int32_t d, uint32_t *adj, int32_t R, uint32_t entry,
-                   int64_t *unreachable0) {
+static int64_t repair_prec(int prec, const float *X, int64_t n, int32_t d, uint32_t *adj, int32_t R,
+                           uint32_t entry, int64_t *unreachable0) {
     unsigned char *reach = (unsigned char *)malloc((size_t)n);
     uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
     if (!reach || !queue) { free(reach); free(queue); return -1; }
@@ -797,7 +805,7 @@ int64_t orc_repair(const float *X, int64_t n, int32_t d, uint32_t *adj, int32_t 
         double bd = INFINITY, bdf = INFINITY;
         for (int64_t r = 0; r < n; ++r) {
             if (!reach[r]) continue;
-            const double dd = dist64(X + (int64_t)u * d, X + r * d, d);
+            const double dd = cdist(prec, X + (int64_t)u * d, X + r * d, d);
             if (adj[r * R + R - 1] == ORC_NONE) {
                 if (dd < bd) { bd = dd; best = r; }
             } else if (dd < bdf) {
@@ -819,6 +827,11 @@ int64_t orc_repair(const float *X, int64_t n, int32_t d, uint32_t *adj, int32_t 
     return repairs;
 }
 
+int64_t orc_repair(const float *X, int64_t n, int32_t d, uint32_t *adj, int32_t R, uint32_t entry,
+                   int64_t *unreachable0) {
+    return repair_prec(0, X, n, d, adj, R, entry, unreachable0);
+}
+
 /*
  * Full construction (Alg. 1): bipartite graph from the training queries'
  * kNN lists, neighbourhood-aware projection (Alg. 2 with Alg. 3),
@@ -833,9 +846,9 @@ int64_t orc_repair(const float *X, int64_t n, int32_t d, uint32_t *adj, int32_t 
  *   stats[8]: pivots, projection reprunes, CE reprunes, repairs,
  *             pj edges, final edges, isolated-in-G_pj, unreachable-before-repair.
  */
-int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
-              const uint32_t *knn, int32_t nqd, int32_t M, int32_t L, uint32_t entry,
-              uint32_t *pj_out, uint32_t *adj_out, int64_t *stats) {
+int orc_build_prec(const float *X, int64_t n, int64_t nt, int32_t d,
+                   const uint32_t *knn, int32_t nqd, int32_t M, int32_t L, uint32_t entry,
+                   uint32_t *pj_out, uint32_t *adj_out, int64_t *stats, int32_t prec) {
     if (n <= 0 || nt < 0 || d <= 0 || nqd < 1 || M <= 0 || L <= 0 || (int64_t)entry >= n)
         return ORC_EINVAL;
     int rc = ORC_ENOMEM;
@@ -875,19 +888,19 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
                 if (c == x || seen[c]) continue;
                 seen[c] = 1;
                 buf[nc].id = c;
-                buf[nc].d = dist64(xv, X + (int64_t)c * d, d);
+                buf[nc].d = cdist(prec, xv, X + (int64_t)c * d, d);
                 ++nc;
             }
         }
         for (int32_t i = 0; i < nc; ++i) seen[buf[i].id] = 0;
         qsort(buf, (size_t)nc, sizeof(ent64), cmp_ent64);
-        int32_t nr = acquire_neighbors(X, d, x, buf, nc, M, 1, res);
+        int32_t nr = acquire_neighbors(prec, X, d, x, buf, nc, M, 1, res);
         Gpj[x].n = 0;                                    /* N'(x) replaces the list */
         for (int32_t i = 0; i < nr; ++i)
             if (ul_push(&Gpj[x], res[i])) goto done;
         for (int32_t i = 0; i < nr; ++i) snap[i] = res[i];
         for (int32_t i = 0; i < nr; ++i)
-            if (reverse_update(X, d, Gpj, snap[i], x, M, 1, buf, res, &proj_reprunes)) goto done;
+            if (reverse_update(prec, X, d, Gpj, snap[i], x, M, 1, buf, res, &proj_reprunes)) goto done;
     }
 
     int64_t isolated = 0;
@@ -909,18 +922,18 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
     if (!pool) goto done;
     for (int64_t xi = 0; xi < n; ++xi) {
         uint32_t x = (uint32_t)xi;
-        int32_t ps = beam_search_f64_lists(X, n, d, Gpj, entry, X + xi * d, L, pool, checked,
+        int32_t ps = beam_search_f64_lists(prec, X, n, d, Gpj, entry, X + xi * d, L, pool, checked,
                                            visited);
         int32_t nc = 0;
         for (int32_t i = 0; i < ps; ++i)
             if (pool[i].id != x) buf[nc++] = pool[i];
-        int32_t nr = acquire_neighbors(X, d, x, buf, nc, M, 0, res);
+        int32_t nr = acquire_neighbors(prec, X, d, x, buf, nc, M, 0, res);
         Gp[x].n = 0;
         for (int32_t i = 0; i < nr; ++i)
             if (ul_push(&Gp[x], res[i])) { free(pool); goto done; }
         for (int32_t i = 0; i < nr; ++i) snap[i] = res[i];
         for (int32_t i = 0; i < nr; ++i)
-            if (reverse_update(X, d, Gp, snap[i], x, M, 0, buf, res, &ce_reprunes)) {
+            if (reverse_update(prec, X, d, Gp, snap[i], x, M, 0, buf, res, &ce_reprunes)) {
                 free(pool);
                 goto done;
             }
@@ -948,7 +961,7 @@ int orc_build(const float *X, int64_t n, int64_t nt, int32_t d,
             adj_out[v * R + j] = j < F[v].n ? F[v].v[j] : ORC_NONE;
     }
     int64_t unreachable0 = 0;
-    repairs = orc_repair(X, n, d, adj_out, R, entry, &unreachable0);
+    repairs = repair_prec(prec, X, n, d, adj_out, R, entry, &unreachable0);
     if (repairs < 0) goto done;
     int64_t fin_edges = 0;
     for (int64_t v = 0; v < n * R; ++v) fin_edges += adj_out[v] != ORC_NONE;
@@ -975,6 +988,11 @@ done:
     free(visited);
     free(checked);
     return rc;
+}
+
+int orc_build(const float *X, int64_t n, int64_t nt, int32_t d, const uint32_t *knn, int32_t nqd, int32_t M,
+              int32_t L, uint32_t entry, uint32_t *pj_out, uint32_t *adj_out, int64_t *stats) {
+    return orc_build_prec(X, n, nt, d, knn, nqd, M, L, entry, pj_out, adj_out, stats, 0);
 }
 
 

@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
     L.roar_build_index.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P, P,
                                    ctypes.POINTER(u32), P, P]
     L.roar_build_index.restype = ctypes.c_int
+    L.roar_build_index_literal.argtypes = [P, i64, i32, P, i64, i32, i32, i32, P, P, ctypes.POINTER(u32), P, P]
+    L.roar_build_index_literal.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -474,6 +476,27 @@ def build_index(X, T, nq_depth=100, M=32, L_build=500, threads=0, stream=None, r
                              pj=_ptr(pj) if pj is not None else None)
     stats = dict(zip(STAT_KEYS, st.tolist()))
     return (adj, entry, stats, pj) if return_pj else (adj, entry, stats)
+
+
+def build_index_literal(X, T, nq_depth=100, M=32, L_build=500, stream=None):
+    """Alg. 1 in its literal order from the library's GPU parts (see
+    roar_build_index_literal): returns (adj int32 [n, 2M], entry, stats,
+    G_pj int32 [n, M]). For checking on small inputs."""
+    import numpy as np
+    import torch
+
+    assert X.is_cuda and T.is_cuda and X.dtype == torch.float32 and T.dtype == torch.float32
+    n, d = X.shape
+    adj = torch.empty((n, 2 * M), dtype=torch.int32, device=X.device)
+    pj = torch.empty((n, M), dtype=torch.int32, device=X.device)
+    st = np.zeros(16, dtype=np.float64)
+    e = ctypes.c_uint32()
+    _check(lib().roar_build_index_literal(_ptr(X), n, d, _ptr(T), T.shape[0], nq_depth, M, L_build, _ptr(adj),
+                                          _ptr(pj), ctypes.byref(e), st.ctypes.data, _stream_ptr(stream)),
+           "roar_build_index_literal")
+    stats = {"total_s": st[0], "pivots": st[6], "pj_edges": st[7], "final_edges": st[8],
+             "unreachable_before_repair": st[9], "repairs": st[10]}
+    return adj, e.value, stats, pj
 
 
 def insert(X, adj, entry, n_old, T, pivot, nout, nout_cnt, M, L, stream=None):

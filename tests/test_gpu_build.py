@@ -98,3 +98,29 @@ def test_build_invariants_and_recall(tiny):
     rec_oracle_graph = oracle.recall_at_k(ref_ids, gt, 10)
     idx.close()
     assert rec >= rec_oracle_graph - 0.05, (rec, rec_oracle_graph)
+
+
+def test_literal_build_matches_oracle_tiny(tiny):
+    """Alg. 1 in its literal order, composed of the library's GPU parts (kNN,
+    search, Alg. 3), against the oracle's construction in the same FP32
+    fixed-order precision from the same kNN lists: G_pj and the final graph
+    identical row for row, the same entry."""
+    import torch
+
+    import paper_2408_08933_gb300 as pkg
+
+    X, T = tiny["X"], tiny["T"]
+    Xd, Td = _cuda(X), _cuda(T)
+    adj, entry, stats, pj = pkg.build_index_literal(Xd, Td, nq_depth=100, M=32, L_build=500)
+    kid, _ = pkg.knn(Td, Xd, 100)
+    torch.cuda.synchronize()
+    knn = kid.cpu().numpy().view(np.uint32)
+    assert entry == oracle.medoid(X)
+    r_adj, r_pj, r_st = oracle.build_index(X, knn, 32, 500, entry, precision="f32")
+    g_pj = pj.cpu().numpy().view(np.uint32)
+    g_adj = adj.cpu().numpy().view(np.uint32)
+    bad_pj = [v for v in range(len(X)) if not np.array_equal(g_pj[v], r_pj[v])]
+    bad_adj = [v for v in range(len(X)) if not np.array_equal(g_adj[v], r_adj[v])]
+    assert not bad_pj, (len(bad_pj), bad_pj[:5])
+    assert not bad_adj, (len(bad_adj), bad_adj[:5])
+    assert (stats["pivots"], stats["repairs"]) == (r_st["pivots"], r_st["repairs"])

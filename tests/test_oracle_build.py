@@ -8,6 +8,7 @@ whole index against.)
 from collections import deque
 
 import numpy as np
+import pytest
 
 import oracle
 from conftest import load_golden
@@ -92,8 +93,11 @@ def test_tiny_search_reaches_exact_result_at_full_L(tiny):
     assert np.all(visits == X.shape[0])
 
 
-def test_projection_hand_traced_on_a_circle():
-    """G_pj of the oracle's construction against a hand-traced case (Alg. 1-3)."""
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_projection_hand_traced_on_a_circle(precision):
+    """G_pj of the oracle's construction against a hand-traced case (Alg. 1-3).
+    Every margin in the case is far above FP32 rounding, so the FP32 form of
+    the construction must take the same decisions."""
     import json
     import os
 
@@ -103,15 +107,17 @@ def test_projection_hand_traced_on_a_circle():
     X = np.zeros((len(r), 4), np.float32)
     X[:, 0], X[:, 1] = np.cos(r), np.sin(r)
     knn = np.asarray(g["knn"], dtype=np.uint32)
-    adj, pj, stats = oracle.build_index(X, knn, g["M"], 10, 0)
+    adj, pj, stats = oracle.build_index(X, knn, g["M"], 10, 0, precision=precision)
     for v, row in g["pj"]:
         got = [int(u) for u in pj[v] if u != 0xFFFFFFFF]
         assert got == row, (v, got, row)
 
 
-def test_construction_hand_traced_on_a_circle():
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_construction_hand_traced_on_a_circle(precision):
     """The oracle's whole construction (projection, connectivity enhancement,
-    final union, repair) against a hand-traced case (Alg. 1-3)."""
+    final union, repair) against a hand-traced case (Alg. 1-3), in FP64 and in
+    the FP32 fixed-order form (margins far above FP32 rounding)."""
     import json
     import os
 
@@ -121,7 +127,7 @@ def test_construction_hand_traced_on_a_circle():
     X = np.zeros((len(r), 4), np.float32)
     X[:, 0], X[:, 1] = np.cos(r), np.sin(r)
     knn = np.asarray(g["knn"], dtype=np.uint32)
-    adj, pj, stats = oracle.build_index(X, knn, g["M"], g["L"], g["entry"])
+    adj, pj, stats = oracle.build_index(X, knn, g["M"], g["L"], g["entry"], precision=precision)
     for v, row in g["pj"]:
         assert [int(u) for u in pj[v] if u != 0xFFFFFFFF] == row, ("pj", v)
     for v, row in g["adj"]:
@@ -142,3 +148,17 @@ def test_hand_traced_reachability_repair():
     # already connected: nothing to do
     adj2, r2, u2 = oracle.repair(X, adj, g["entry"])
     assert adj2.tolist() == adj.tolist() and (r2, u2) == (0, 0)
+
+
+def test_fp32_construction_close_to_fp64(tiny):
+    """The FP32 fixed-order construction on the tiny workload: the same
+    invariants, and nearly the same graph as FP64 (decisions differ only
+    where two distances fall within FP32 rounding)."""
+    X, knn = tiny["X"], tiny["knn"]
+    adj32, pj32, st32 = oracle.build_index(X, knn, 32, 500, tiny["entry"], precision="f32")
+    adj64, pj64 = tiny["adj"], tiny["pj"]
+    same_pj = np.mean([np.array_equal(a, b) for a, b in zip(pj32, pj64)])
+    same_adj = np.mean([np.array_equal(a, b) for a, b in zip(adj32, adj64)])
+    assert same_pj > 0.95 and same_adj > 0.9, (same_pj, same_adj)
+    deg = (adj32 != NONE).sum(1)
+    assert deg.max() <= 64 and st32["unreachable_before_repair"] >= 0
