@@ -625,11 +625,34 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
         R = adj_old.shape[1]
         adj_u = torch.full((n, R), -1, dtype=torch.int32, device=dev)
         adj_u[:n_old] = adj_old
+        # The windowed insertion equals the one-row-at-a-time order (window 1):
+        # check on the first rows inserted, at the full graph size.
+        m_chk = min(2000, n - n_old)
+        chk = {}
+        for win in (1, args.insert_window):
+            a_c = adj_u[:n_old + m_chk].clone()
+            no_c, cn_c = nout.copy(), cnt.copy()
+            t0 = time.time()
+            q_c = pkg.insert(Xd[:n_old + m_chk], a_c, entry_old, n_old, T, knn_h[:, 0], no_c, cn_c, 32, 100,
+                             window=win)
+            torch.cuda.synchronize()
+            chk[win] = (a_c.cpu().numpy(), no_c, cn_c, q_c, time.time() - t0)
+            del a_c
+        a1, a2 = chk[1], chk[args.insert_window]
+        window_check = {"rows": int(m_chk), "identical": bool(np.array_equal(a1[0], a2[0]) and
+                                                             np.array_equal(a1[1], a2[1]) and
+                                                             np.array_equal(a1[2], a2[2]) and
+                                                             np.array_equal(a1[3], a2[3])),
+                        "rows_per_s_window_1": m_chk / a1[4],
+                        f"rows_per_s_window_{args.insert_window}": m_chk / a2[4]}
+        del chk, a1, a2
+        log(f"window check {window_check}")
         t0 = time.time()
-        chosen = pkg.insert(Xd, adj_u, entry_old, n_old, T, knn_h[:, 0], nout, cnt, 32, 100)
+        chosen, ins_st = pkg.insert(Xd, adj_u, entry_old, n_old, T, knn_h[:, 0], nout, cnt, 32, 100,
+                                    window=args.insert_window, return_stats=True)
         torch.cuda.synchronize()
         ins_s = time.time() - t0
-        log(f"inserted {n - n_old} rows in {ins_s:.1f}s")
+        log(f"inserted {n - n_old} rows in {ins_s:.1f}s {ins_st}")
         del T
         table = {}
         for gname, (a_, e_) in {"updated": (adj_u, entry_old), "rebuilt": (adj, entry)}.items():
@@ -664,7 +687,8 @@ def _extra_mode(args, w, torch, pkg, rs, dev, X, Q, Xd, Qd, adj, entry, gt, bsta
                              "deleted_in_answers": int(dead[ih[ih != 0xFFFFFFFF]].sum())}
         gidx.close()
         res.update({"n_old": int(n_old), "inserted": int(n - n_old), "build_old_s": build_s,
-                    "insert_s": ins_s, "inserts_per_s": (n - n_old) / ins_s,
+                    "insert_s": ins_s, "inserts_per_s": (n - n_old) / ins_s, "insert_window": args.insert_window,
+                    "insert_work": ins_st, "window_check": window_check,
                     "rows_with_a_connected_query": float((chosen >= 0).mean()),
                     "search": table, "tombstones_10pct": trows})
     elif args.mode == "serving":
@@ -711,6 +735,7 @@ def main():
                     help="run the uneven batch and the serving loop on the main workload's index and skip "
                          "the 10M x 512 precision workload")
     ap.add_argument("--n-comp", type=int, default=0, help="override the mixture components (small experiments)")
+    ap.add_argument("--insert-window", type=int, default=256, help="rows per speculative insertion window (update mode)")
     ap.add_argument("--offset-norm", type=float, default=0.0,
                     help="override the OOD offset norm (ood mode experiments; the workloads use 1.5)")
     ap.add_argument("--mode", default="main", choices=["main", "precision", "uneven", "serving", "ood", "ablation", "update"],

@@ -487,15 +487,23 @@ roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const flo
 
 /*
  * Insertion through the saved bipartite graph (Sec. 5.7): rows n_old ..
- * n_total-1 of X_dev join the graph one at a time, in id order. For row v: a
- * beam search (width L, visit cap 16384) of X[v]; the first pool entry that a
- * training query is connected to (it is in that query's N_out, or it is the
- * query's pivot); q = the connected query nearest to v; v's out-list =
- * AcquireNeighbors with fill (Alg. 3, bound M) over N_out(q), or over the
- * search pool when no pool entry is connected; each listed p gets p -> v,
- * appended when p's row has room, else p's row and v re-pruned to R with
- * Alg. 3 (fill); v then joins N_out(q) while it has room. All decisions use
- * FP32 distances in the search's fixed summation order.
+ * n_total-1 of X_dev join the graph with the result of inserting them one at
+ * a time, in id order. For row v: a beam search (width L, visit cap 16384) of
+ * X[v]; the first pool entry that a training query is connected to (it is in
+ * that query's N_out, or it is the query's pivot); q = the connected query
+ * nearest to v; v's out-list = AcquireNeighbors with fill (Alg. 3, bound M)
+ * over N_out(q), or over the search pool when no pool entry is connected;
+ * each listed p gets p -> v, appended when p's row has room, else p's row and
+ * v re-pruned to R with Alg. 3 (fill); v then joins N_out(q) while it has
+ * room. All decisions use FP32 distances in the search's fixed summation
+ * order.
+ * The rows are processed in windows of `window` rows: their searches run in
+ * one launch on the graph as it stands and record the nodes they expand; rows
+ * are then applied in order while no node a row's search expanded has changed
+ * since that search ran (then the search is the one the sequential order
+ * runs); the first row that fails is searched again in the next window. So
+ * the result never depends on `window`; window = 1 is the plain sequential
+ * order.
  *   X_dev        device [n_total][d] FP32 rows (the new rows already written).
  *   adj_dev      device [n_total][R] graph; rows >= n_old must be empty
  *                (ROAR_NONE_ID); updated in place. R <= 64, 1 <= M <= R.
@@ -504,13 +512,26 @@ roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const flo
  *   pivot_host   host [nt]: each query's nearest base row.
  *   nout_host    host [nt][nout_cap] N_out lists, nout_cnt_host [nt] their
  *                lengths (nout_cap <= 1024); updated in place.
+ *   window       rows per window, 1 .. 4096.
  *   chosen_q_host host [n_total - n_old] out: q per new row, or -1.
- * Synchronises `stream`. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ *   stats        host [15] out or NULL: windows, searches run (rows searched
+ *                more than once count each time), Alg. 3 lists computed,
+ *                lists recomputed because N_out(q) grew, re-prune batches,
+ *                rows re-pruned; then host seconds spent in setup (graph
+ *                copy, connection lists, buffers), searches, lists, applying
+ *                rows (re-prunes included), re-prunes, device graph updates
+ *                and connected-query picks; then the windows whose apply
+ *                stopped at a search that expanded a rewritten row, and
+ *                those where every changed row it expanded was only appended
+ *                to.
+ * Synchronises `stream`. Uses about n_total * (R * 4 + 48) bytes of host
+ * memory plus the connection lists, and a device copy of T_host. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
  */
 roar_status roar_insert(const float *X_dev, int64_t n_total, int32_t d, uint32_t *adj_dev, int32_t R,
                         uint32_t entry, int64_t n_old, const float *T_host, int64_t nt,
                         const uint32_t *pivot_host, uint32_t *nout_host, int32_t *nout_cnt_host,
-                        int32_t nout_cap, int32_t M, int32_t L, int32_t *chosen_q_host, void *stream);
+                        int32_t nout_cap, int32_t M, int32_t L, int32_t window, int32_t *chosen_q_host,
+                        double *stats, void *stream);
 
 #ifdef __cplusplus
 }

@@ -102,7 +102,7 @@ def lib() -> ctypes.CDLL:
     L.roar_medoid.restype = ctypes.c_int
     L.roar_acquire.argtypes = [P, i64, i32, P, i64, P, i32, P, i32, i32, P, P, P, P]
     L.roar_acquire.restype = ctypes.c_int
-    L.roar_insert.argtypes = [P, i64, i32, P, i32, u32, i64, P, i64, P, P, P, i32, i32, i32, P, P]
+    L.roar_insert.argtypes = [P, i64, i32, P, i32, u32, i64, P, i64, P, P, P, i32, i32, i32, i32, P, P, P]
     L.roar_insert.restype = ctypes.c_int
     L.roar_build_index.argtypes = [P, i64, i32, P, i64, i32, i32, i32, i32, P, P,
                                    ctypes.POINTER(u32), P, P]
@@ -499,12 +499,15 @@ def build_index_literal(X, T, nq_depth=100, M=32, L_build=500, stream=None):
     return adj, e.value, stats, pj
 
 
-def insert(X, adj, entry, n_old, T, pivot, nout, nout_cnt, M, L, stream=None):
+def insert(X, adj, entry, n_old, T, pivot, nout, nout_cnt, M, L, window=256, stream=None, return_stats=False):
     """Insert rows n_old.. of CUDA X [n, d] into the CUDA graph adj [n, R]
-    (int32, rows >= n_old all -1) through the saved bipartite graph (Sec. 5.7).
-    T: host float32 [nt, d]; pivot: host uint32 [nt]; nout: host uint32
-    [nt, cap] and nout_cnt: host int32 [nt], updated in place. Returns the
-    chosen query per new row (numpy int32, -1 when none)."""
+    (int32, rows >= n_old all -1) through the saved bipartite graph (Sec. 5.7),
+    with the result of inserting them one at a time; `window` rows are
+    searched per launch (the result does not depend on it). T: host float32
+    [nt, d]; pivot: host uint32 [nt]; nout: host uint32 [nt, cap] and
+    nout_cnt: host int32 [nt], updated in place. Returns the chosen query per
+    new row (numpy int32, -1 when none), and with return_stats a dict of the
+    work done."""
     import numpy as np
 
     n, d = X.shape
@@ -512,10 +515,16 @@ def insert(X, adj, entry, n_old, T, pivot, nout, nout_cnt, M, L, stream=None):
     pivot = np.ascontiguousarray(pivot, dtype=np.uint32)
     assert nout.dtype == np.uint32 and nout.flags.c_contiguous and nout_cnt.dtype == np.int32
     chosen = np.full(n - n_old, -1, dtype=np.int32)
+    st = np.zeros(15, dtype=np.float64)
     _check(lib().roar_insert(_ptr(X), n, d, _ptr(adj), adj.shape[1], entry, n_old, T.ctypes.data, T.shape[0],
                              pivot.ctypes.data, nout.ctypes.data, nout_cnt.ctypes.data, nout.shape[1], M, L,
-                             chosen.ctypes.data, _stream_ptr(stream)), "roar_insert")
-    return chosen
+                             int(window), chosen.ctypes.data, st.ctypes.data, _stream_ptr(stream)), "roar_insert")
+    if not return_stats:
+        return chosen
+    keys = ("windows", "searches", "lists", "lists_redone", "reprune_batches", "rows_repruned", "setup_s",
+            "search_s", "lists_s", "apply_s", "reprune_s", "scatter_s", "pick_s", "stops_rewritten",
+            "stops_appended")
+    return chosen, dict(zip(keys, st.tolist()))
 
 
 def acquire(X, xs, cand, ncand, M, fill, sorted_out=False, stream=None):

@@ -89,6 +89,11 @@ struct SearchArgs {
     const int64_t *bi_off;
     const uint32_t *bi_q;
     int64_t bi_nt;
+    // Optional expansion trace (batch launches, null otherwise): the first
+    // trace_cap nodes a query expands, in order, at trace[qi * trace_cap ..];
+    // `hops` tells how many there were.
+    uint32_t *trace;
+    int32_t trace_cap;
 };
 
 // Shared memory of one warp: pool (8 B per slot), candidate buffers (16 B per

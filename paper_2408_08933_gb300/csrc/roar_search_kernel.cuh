@@ -676,6 +676,8 @@ beam_search_kernel(const SearchArgs a) {
                         __syncwarp();
                         if (lane == 0) pi[sel] = v | kChecked;
                         ++hops;
+                        if (a.trace && lane == 0 && hops <= (uint32_t)a.trace_cap)
+                            a.trace[qi * (int64_t)a.trace_cap + hops - 1] = v;
                         cursor = sel + 1;
                         if constexpr (BI) {
                             bi_j = a.bi_off[v];

@@ -35,10 +35,12 @@ def test_insert_rejects_bad_sizes(lib):
         dict(n_total=80, d=64, R=8, entry=0, n_old=90, M=4, L=64, cap=64),      # fewer rows than before
         dict(n_total=100, d=64, R=8, entry=0, n_old=90, M=4, L=64, cap=2000),   # N_out capacity
         dict(n_total=100, d=66, R=8, entry=0, n_old=90, M=4, L=64, cap=64),     # d % 4
+        dict(n_total=100, d=64, R=8, entry=0, n_old=90, M=4, L=64, cap=64, win=0),     # window
+        dict(n_total=100, d=64, R=8, entry=0, n_old=90, M=4, L=64, cap=64, win=5000),  # window
     ]
     for c in cases:
         rc = lib.roar_insert(fake, c["n_total"], c["d"], fake, c["R"], c["entry"], c["n_old"], fake, 10, fake,
-                             fake, fake, c["cap"], c["M"], c["L"], fake, None)
+                             fake, fake, c["cap"], c["M"], c["L"], c.get("win", 64), fake, None, None)
         assert rc == EINVAL, c
         assert "roar_insert" in _msg(lib)
 
