@@ -396,8 +396,9 @@ roar_status roar_quantize(const float *X, int64_t n, int32_t d, roar_dtype dtype
  *   T [nt][d], X [n][d]   device FP32, 16-byte aligned, d % 8 == 0, d <= 512.
  *   kk                    1..128, kk <= n.
  *   ids, dist             device [nt][kk] outputs.
- * Allocates and frees its own device scratch (BF16 copies of T and X and
- * candidate buffers of 8 KB per query row for up to 131,072 rows at a time)
+ * Allocates and frees its own device scratch (BF16 copies of T and X with
+ * rows padded to a multiple of 64 columns, and candidate buffers of 8 KB per
+ * query row for up to 131,072 rows at a time)
  * and synchronises `stream` before returning. Errors: ROAR_EINVAL,
  * ROAR_ENOMEM, ROAR_ECUDA, ROAR_ETIMEOUT (a bounded tensor-core wait gave up).
  */

@@ -47,6 +47,19 @@ __global__ void quantize_bf16_kernel(const float *__restrict__ X, int64_t n, int
     for (int i = lane; i < d; i += 32) o[i] = __float2bfloat16_rn(x[i]);
 }
 
+// One warp per row: BF16 rows padded with zeros to dp columns (the kNN
+// kernel's operands: rows of whole 64-column K chunks, so each chunk of a row
+// is one aligned 128-byte segment).
+__global__ void quantize_bf16_pad_kernel(const float *__restrict__ X, int64_t n, int d, int dp,
+                                         __nv_bfloat16 *__restrict__ out) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float *x = X + row * d;
+    __nv_bfloat16 *o = out + row * dp;
+    for (int i = lane; i < dp; i += 32) o[i] = i < d ? __float2bfloat16_rn(x[i]) : __float2bfloat16_rn(0.0f);
+}
+
 // One warp per row. FP8-E4M3: s = maxabs / 448 (IEEE division), code = E4M3(x / s)
 // rounded to nearest even and saturated to +-448; an all-zero row gets s = 1.
 __global__ void quantize_fp8_kernel(const float *__restrict__ X, int64_t n, int d,
@@ -115,9 +128,9 @@ __global__ void rescore_kernel(const float *__restrict__ T, int64_t nt, const fl
 
 }  // namespace
 
-roar_status quantize_bf16(const float *X, int64_t n, int d, void *out, cudaStream_t s) {
+roar_status quantize_bf16_pad(const float *X, int64_t n, int d, int dp, void *out, cudaStream_t s) {
     const int64_t blocks = (n + 7) / 8;
-    quantize_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, (__nv_bfloat16 *)out);
+    quantize_bf16_pad_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, dp, (__nv_bfloat16 *)out);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ROAR_OK : cuda_fail(e, "quantize_bf16");
 }
@@ -147,10 +160,10 @@ extern "C" roar_status roar_quantize(const float *X, int64_t n, int32_t d, roar_
 }
 
 namespace roar {
-size_t knn_tc_smem_bytes(int d);
 cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloat16 *X16, int64_t n, int d,
                           int C, int cap, float *buf_s, uint32_t *buf_i, uint32_t *cand, int *err,
                           uint64_t wait_ns, cudaStream_t s);
+int64_t knn_tc_wave_rows(int d);
 // Wall-time limit of each bounded wait in the tensor-core kernel: 2 s by
 // default, far above any legitimate wait there.
 constexpr int64_t kKnnWaitDefaultNs = 2000000000ll;
@@ -173,7 +186,11 @@ extern "C" roar_status roar_knn(const float *T, int64_t nt, const float *X, int6
     if (nt == 0) return ROAR_OK;
     if (!T || !X || !ids || !dist || !aligned(T, 16) || !aligned(X, 16)) return ROAR_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t RB = std::min<int64_t>(nt, 131072);  // query rows per launch
+    const int dp = (d + 63) / 64 * 64;   // BF16 operand rows padded to whole 64-column K chunks
+    // Query rows per launch: whole waves of the kernel, about 131,072 at most
+    // (a partial last wave leaves SMs idle for a whole sweep of X).
+    const int64_t wave = knn_tc_wave_rows(dp);
+    const int64_t RB = std::min<int64_t>(nt, std::max<int64_t>(wave, 131072 / wave * wave));
     __nv_bfloat16 *t16 = nullptr, *x16 = nullptr;
     float *bs = nullptr;
     uint32_t *bi = nullptr, *cand = nullptr;
@@ -181,8 +198,8 @@ extern "C" roar_status roar_knn(const float *T, int64_t nt, const float *X, int6
     const uint64_t wait_ns = (uint64_t)g_knn_wait_ns.load();
     roar_status rc = ROAR_OK;
     int herr = 0;
-    cudaError_t e = cudaMalloc(&t16, (size_t)nt * d * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&x16, (size_t)n * d * 2);
+    cudaError_t e = cudaMalloc(&t16, (size_t)nt * dp * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&x16, (size_t)n * dp * 2);
     if (e == cudaSuccess) e = cudaMalloc(&bs, (size_t)RB * CAP * 4);
     if (e == cudaSuccess) e = cudaMalloc(&bi, (size_t)RB * CAP * 4);
     if (e == cudaSuccess) e = cudaMalloc(&cand, (size_t)RB * C * 4);
@@ -194,11 +211,11 @@ extern "C" roar_status roar_knn(const float *T, int64_t nt, const float *X, int6
         rc = ROAR_ENOMEM;
         goto done;
     }
-    if ((rc = quantize_bf16(T, nt, d, t16, s)) != ROAR_OK) goto done;
-    if ((rc = quantize_bf16(X, n, d, x16, s)) != ROAR_OK) goto done;
+    if ((rc = quantize_bf16_pad(T, nt, d, dp, t16, s)) != ROAR_OK) goto done;
+    if ((rc = quantize_bf16_pad(X, n, d, dp, x16, s)) != ROAR_OK) goto done;
     for (int64_t r0 = 0; r0 < nt; r0 += RB) {
         const int64_t rb = std::min(RB, nt - r0);
-        e = knn_tc_launch(t16 + r0 * d, rb, x16, n, d, C, CAP, bs, bi, cand, err, wait_ns, s);
+        e = knn_tc_launch(t16 + r0 * dp, rb, x16, n, dp, C, CAP, bs, bi, cand, err, wait_ns, s);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "roar_knn: tensor-core scores");
             goto done;

@@ -2,8 +2,10 @@
 // construction, Sec. 4.2.1): S = T . X^T in BF16 with FP32 accumulation on the
 // 5th-generation tensor cores, never written to memory.
 //
-// One CTA owns 128 rows of T (the MMA's M) and keeps them resident in shared
-// memory; it sweeps all rows of X in tiles of 256 (the MMA's N). Warp roles:
+// One CTA owns 128 or 256 rows of T and keeps them resident in shared memory;
+// it sweeps all rows of X in tiles of 256 or 128 (the MMA's N). With 256 rows
+// (d <= 256) the two 128-row halves (the MMA's M is 128) share each X tile,
+// which halves the X bytes every score needs from L2. Warp roles:
 // two producer warps stage 64-wide K chunks of X through a ring of up to four
 // shared-memory stages (cp.async with zero fill past n and d) in the canonical
 // no-swizzle K-major layout (8 x 16-byte core matrices, K-adjacent ones 128 B
@@ -24,6 +26,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 
@@ -35,25 +38,29 @@ roar_status cuda_fail(cudaError_t e, const char *what);
 
 namespace {
 
-constexpr int kTM = 128;           // T rows per CTA (MMA M)
-constexpr int kTN = 256;           // X rows per tile (MMA N)
+constexpr int kTM = 128;           // T rows per MMA (its M); a CTA holds kMH such halves
 constexpr int kKC = 64;            // K elements per staged chunk (128 bytes per row)
 constexpr int kProducers = 64;     // warps 0-1 stage operands
 constexpr int kMmaWarp = 2;        // lane 0 issues the MMAs; the warp owns TMEM
-constexpr int kThreads = 7 * 32;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 8;
 constexpr int kCap = 1024;         // candidate buffer entries per row
 constexpr uint64_t kDrainNs = 2000000000ull;  // bound of the final wait for issued MMAs
-constexpr int kTmemCols = 512;     // two 256-column accumulators
-constexpr uint32_t kChunkA = kTM * kKC * 2;   // 16 KB
-constexpr uint32_t kChunkB = kTN * kKC * 2;   // 32 KB
+constexpr int kTmemCols = 512;     // 2 buffers x kMH halves x (256 / kMH) columns
+constexpr uint32_t kChunkA = kTM * kKC * 2;   // 16 KB: one half's 64-wide K chunk
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
-// M >> 4 at bit 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
-                            ((uint32_t)(kTM >> 4) << 24);
+// X rows per tile (the MMA's N), threads and B chunk bytes for kMH halves.
+template <int kMH>
+struct KnnShape {
+    static constexpr int TN = 256 / kMH;
+    static constexpr int threads = (3 + 4 * kMH) * 32;
+    static constexpr uint32_t chunkB = (uint32_t)TN * kKC * 2;
+    // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+    // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+    // M >> 4 at bit 24.
+    static constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                      ((uint32_t)(kTM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -194,11 +201,12 @@ __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -312,18 +320,24 @@ __device__ __forceinline__ void stage_chunk(uint32_t dst, const __nv_bfloat16 *s
 
 // Warp roles: 0-1 stage operands (cp.async, completion on per-stage "full"
 // barriers), 2 issues the MMAs (lane 0; stage freed through "empty" barriers
-// by tcgen05.commit) and owns TMEM, 3-6 read the two alternating 256-column
-// accumulators (rows 32 * (warp % 4) + lane) while the next tile is computed.
+// by tcgen05.commit) and owns TMEM, 3 .. 3 + 4 kMH - 1 read the two
+// alternating accumulators while the next tile is computed: warp w reads TMEM
+// lanes 32 * (w % 4) .. + 31 of half (w - 3) / 4, one T row per thread.
 // kTma: operands staged by TMA (one thread issues 2-D tensor-map copies into
 // the 128-byte-swizzled layout, completion counted in bytes on the "full"
 // barriers) instead of the two cp.async producer warps and the no-swizzle
-// layout.
-template <bool kTma>
-__global__ void __launch_bounds__(kThreads, 1)
+// layout. kMH: 128-row halves of T per CTA (2 needs kTma).
+template <bool kTma, int kMH>
+__global__ void __launch_bounds__(KnnShape<kMH>::threads, 1)
 knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat16 *__restrict__ X,
               int64_t n, int d, int stages, int C, float *__restrict__ buf_s,
               uint32_t *__restrict__ buf_i, uint32_t *__restrict__ out_i, int *__restrict__ err,
-              uint64_t wait_ns, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+              uint64_t wait_ns, const __grid_constant__ CUtensorMap tmA,
+              const __grid_constant__ CUtensorMap tmB) {
+    static_assert(kTma || kMH == 1, "the cp.async producers stage one half");
+    constexpr int kTN = KnnShape<kMH>::TN;
+    constexpr uint32_t kChunkB = KnnShape<kMH>::chunkB;
+    constexpr uint32_t kIdesc = KnnShape<kMH>::idesc;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], acc_full[2], acc_empty[2], a_full, drain_bar;
     __shared__ uint32_t tmem_slot;
@@ -334,10 +348,11 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
     const int nkc = (d + kKC - 1) / kKC;
     // TMA's 128-byte swizzle repeats every 1024 bytes: start the operands there.
     const uint32_t a_base = kTma ? ((smem_addr(smem) + 1023u) & ~1023u) : smem_addr(smem);
-    const uint32_t b_base = a_base + (uint32_t)nkc * kChunkA;
-    const int64_t m0 = (int64_t)blockIdx.x * kTM;
+    const uint32_t b_base = a_base + (uint32_t)(nkc * kMH) * kChunkA;
+    const int64_t m0 = (int64_t)blockIdx.x * (kTM * kMH);
     const int64_t ntiles = (n + kTN - 1) / kTN;
     const int64_t nchunks = ntiles * nkc;
+
 
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -346,7 +361,7 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4 * 32);
+            mbar_init(&acc_empty[b], 4 * 32 * kMH);
         }
         mbar_init(&a_full, kTma ? 1 : kProducers);
         mbar_init(&drain_bar, 1);
@@ -366,26 +381,44 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
     if (kTma && warp < 2) {
         // ---- producer: one thread issues every TMA copy ----
         if (warp == 0 && lane == 0) {
-            int64_t last_g[kMaxStages];
-            for (int s = 0; s < kMaxStages; ++s) last_g[s] = -1;
-            mbar_expect_tx(&a_full, (uint32_t)nkc * kChunkA);
-            for (int c = 0; c < nkc; ++c) tma_load_2d(a_base + (uint32_t)c * kChunkA, &tmA, c * kKC, (int32_t)m0, &a_full);
+            // Per stage: armed at least once, and the parity of the last phase armed.
+            bool armed[kMaxStages];
+            uint32_t last_par[kMaxStages];
+            for (int i = 0; i < kMaxStages; ++i) {
+                armed[i] = false;
+                last_par[i] = 0;
+            }
+            mbar_expect_tx(&a_full, (uint32_t)(nkc * kMH) * kChunkA);
+            for (int c = 0; c < nkc; ++c)
+                for (int h = 0; h < kMH; ++h)
+                    tma_load_2d(a_base + (uint32_t)(c * kMH + h) * kChunkA, &tmA, c * kKC, (int32_t)(m0 + kTM * h),
+                                &a_full);
+            // Chunk g is K chunk c of tile t in stage s, the stage's use number
+            // `wrap`: counters, not divisions (64-bit division is slow).
+            int s = 0, c = 0;
+            uint32_t wrap = 0;
+            int64_t t = 0;
             for (int64_t g = 0; g < nchunks; ++g) {
-                const int s = (int)(g % stages);
-                const uint32_t use = (uint32_t)(g / stages);
-                if (use > 0 && !mbar_wait(&empty_bar[s], (use - 1) & 1, abort_v, wait_ns)) break;
-                const int64_t t = g / nkc;
-                const int c = (int)(g - t * nkc);
+                if (wrap > 0 && !mbar_wait(&empty_bar[s], (wrap - 1) & 1, abort_v, wait_ns)) break;
                 mbar_expect_tx(&full_bar[s], kChunkB);
                 tma_load_2d(b_base + (uint32_t)s * kChunkB, &tmB, c * kKC, (int32_t)(t * kTN), &full_bar[s]);
-                last_g[s] = g;
+                armed[s] = true;
+                last_par[s] = wrap & 1;
+                if (++c == nkc) {
+                    c = 0;
+                    ++t;
+                }
+                if (++s == stages) {
+                    s = 0;
+                    ++wrap;
+                }
             }
             // No copy may still be landing when the CTA exits (after an abort
             // some armed stages are never consumed): wait, bounded, for the
             // last phase armed on every barrier.
             bool drained = mbar_drain(&a_full, 0);
-            for (int s = 0; s < stages; ++s)
-                if (last_g[s] >= 0) drained = mbar_drain(&full_bar[s], (uint32_t)(last_g[s] / stages) & 1) && drained;
+            for (int i = 0; i < stages; ++i)
+                if (armed[i]) drained = mbar_drain(&full_bar[i], last_par[i]) && drained;
             if (!drained) *abort_v = 1;
         }
         __syncwarp();
@@ -393,14 +426,21 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
         // ---- producers ----
         for (int c = 0; c < nkc; ++c) stage_chunk(a_base + (uint32_t)c * kChunkA, T, m0, kTM, nt, d, c * kKC, tid, kProducers);
         cp_async_arrive(&a_full);
+        int s = 0, c = 0;
+        uint32_t wrap = 0;
+        int64_t t = 0;
         for (int64_t g = 0; g < nchunks; ++g) {
-            const int s = (int)(g % stages);
-            const uint32_t use = (uint32_t)(g / stages);
-            if (use > 0 && !mbar_wait(&empty_bar[s], (use - 1) & 1, abort_v, wait_ns)) break;
-            const int64_t t = g / nkc;
-            const int c = (int)(g - t * nkc);
+            if (wrap > 0 && !mbar_wait(&empty_bar[s], (wrap - 1) & 1, abort_v, wait_ns)) break;
             stage_chunk(b_base + (uint32_t)s * kChunkB, X, t * kTN, kTN, n, d, c * kKC, tid, kProducers);
             cp_async_arrive(&full_bar[s]);
+            if (++c == nkc) {
+                c = 0;
+                ++t;
+            }
+            if (++s == stages) {
+                s = 0;
+                ++wrap;
+            }
         }
         cp_async_wait<0>();
     } else if (warp == kMmaWarp) {
@@ -409,31 +449,41 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
             bool issued = false;
             if (mbar_wait(&a_full, 0, abort_v, wait_ns)) {
                 if (!kTma) fence_async_smem();  // cp.async data, written through the generic proxy, to the tensor core
-                int64_t g = 0;
+                // Descriptors of the operand bases; a chunk, a half or a K step
+                // moves the start address field (bytes >> 4).
+                const uint64_t adesc0 = kTma ? smem_desc_sw128(a_base) : smem_desc(a_base, 128, 1024);
+                const uint64_t bdesc0 = kTma ? smem_desc_sw128(b_base) : smem_desc(b_base, 128, 1024);
+                constexpr uint32_t kStep = kTma ? 32 >> 4 : 256 >> 4;   // one K step of 16
+                int s = 0;
+                uint32_t wrap = 0;
                 bool ok = true;
                 for (int64_t t = 0; t < ntiles && ok; ++t) {
                     const int b = (int)(t & 1);
                     const uint32_t ub = (uint32_t)(t >> 1);
                     if (ub > 0 && !mbar_wait(&acc_empty[b], (ub - 1) & 1, abort_v, wait_ns)) break;
                     tc_fence_after();
-                    for (int c = 0; c < nkc; ++c, ++g) {
-                        const int s = (int)(g % stages);
-                        if (!mbar_wait(&full_bar[s], (uint32_t)(g / stages) & 1, abort_v, wait_ns)) {
+                    for (int c = 0; c < nkc; ++c) {
+                        if (!mbar_wait(&full_bar[s], wrap & 1, abort_v, wait_ns)) {
                             ok = false;
                             break;
                         }
                         if (!kTma) fence_async_smem();
                         tc_fence_after();
-                        const uint32_t a_chunk = a_base + (uint32_t)c * kChunkA;
-                        const uint32_t b_chunk = b_base + (uint32_t)s * kChunkB;
+                        const uint64_t bd0 = bdesc0 + (((uint32_t)s * kChunkB) >> 4);
+                        const uint64_t ad0 = adesc0 + (((uint32_t)(c * kMH) * kChunkA) >> 4);
 #pragma unroll
                         for (int ks = 0; ks < kKC / 16; ++ks) {
-                            const uint64_t ad = kTma ? smem_desc_sw128(a_chunk + ks * 32) : smem_desc(a_chunk + ks * 256, 128, 1024);
-                            const uint64_t bd = kTma ? smem_desc_sw128(b_chunk + ks * 32) : smem_desc(b_chunk + ks * 256, 128, 1024);
-                            tc_mma(tmem + (uint32_t)(b * kTN), ad, bd, (c > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+                            for (int h = 0; h < kMH; ++h)
+                                tc_mma(tmem + (uint32_t)((b * kMH + h) * kTN), ad0 + h * (kChunkA >> 4) + ks * kStep,
+                                       bd0 + ks * kStep, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
                         }
                         issued = true;
                         tc_commit(&empty_bar[s]);
+                        if (++s == stages) {
+                            s = 0;
+                            ++wrap;
+                        }
                     }
                     if (ok) tc_commit(&acc_full[b]);
                 }
@@ -453,7 +503,8 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
         // once it could not take another full tile; the cut raises the row's
         // threshold. The accumulator is released before the cuts run.
         const int q = warp & 3;
-        const int64_t wrow0 = m0 + 32 * q;
+        const int half = (warp - 3) >> 2;
+        const int64_t wrow0 = m0 + kTM * half + 32 * q;
         const int64_t row = wrow0 + lane;
         const bool row_ok = row < nt;
         float *rs = buf_s + (row_ok ? row : 0) * (int64_t)kCap;
@@ -471,45 +522,61 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
             tc_fence_after();
             const int64_t n0 = t * kTN;
             const int lim = (int)((n - n0) < kTN ? (n - n0) : kTN);
+            // kGW columns per TMEM read (loads in flight together, one wait):
+            // 128 with two halves (two epilogue warps per SM sub-partition),
+            // 64 with one (measured faster on GB300 for each shape).
+            constexpr int kGW = kMH == 2 ? 128 : 64;
 #pragma unroll 1
-            for (int cb = 0; cb < kTN; cb += 64) {
-                uint32_t ra[32], rb[32];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTN + cb);
-                tc_ld32_issue(taddr, ra);
-                tc_ld32_issue(taddr + 32, rb);
-                tc_wait_ld(ra);
-                reg_after_wait(rb);
+            for (int cb = 0; cb < kTN; cb += kGW) {
+                uint32_t r0[32], r1[32], r2[32], r3[32];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((b * kMH + half) * kTN + cb);
+                tc_ld32_issue(taddr, r0);
+                tc_ld32_issue(taddr + 32, r1);
+                if constexpr (kGW == 128) {
+                    tc_ld32_issue(taddr + 64, r2);
+                    tc_ld32_issue(taddr + 96, r3);
+                }
+                tc_wait_ld(r0);
+                reg_after_wait(r1);
+                if constexpr (kGW == 128) {
+                    reg_after_wait(r2);
+                    reg_after_wait(r3);
+                }
                 if (!row_ok) continue;
-                // Most 64-column groups hold nothing above the row's threshold
+                // Most column groups hold nothing above the row's threshold
                 // once the first tiles have set it: test their maximum first.
                 float mp[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) mp[i] = fmaxf(__uint_as_float(ra[i]), __uint_as_float(rb[i]));
+                for (int i = 0; i < 8; ++i) {
+                    mp[i] = fmaxf(__uint_as_float(r0[i]), __uint_as_float(r1[i]));
+                    if constexpr (kGW == 128)
+                        mp[i] = fmaxf(mp[i], fmaxf(__uint_as_float(r2[i]), __uint_as_float(r3[i])));
+                }
 #pragma unroll
-                for (int j = 8; j < 32; ++j) {
-                    mp[j & 7] = fmaxf(mp[j & 7], __uint_as_float(ra[j]));
-                    mp[j & 7] = fmaxf(mp[j & 7], __uint_as_float(rb[j]));
+                for (int i = 8; i < 32; ++i) {
+                    mp[i & 7] = fmaxf(mp[i & 7], fmaxf(__uint_as_float(r0[i]), __uint_as_float(r1[i])));
+                    if constexpr (kGW == 128)
+                        mp[i & 7] = fmaxf(mp[i & 7], fmaxf(__uint_as_float(r2[i]), __uint_as_float(r3[i])));
                 }
                 const float m = fmaxf(fmaxf(fmaxf(mp[0], mp[1]), fmaxf(mp[2], mp[3])),
                                       fmaxf(fmaxf(mp[4], mp[5]), fmaxf(mp[6], mp[7])));
                 if (!(m > thr)) continue;
+                auto take = [&](const uint32_t (&rr)[32], int c0) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float v = __uint_as_float(ra[j]);
-                    if (v > thr && cb + j < lim) {
-                        rs[cnt] = v;
-                        ri[cnt] = (uint32_t)(n0 + cb + j);
-                        ++cnt;
+                    for (int i = 0; i < 32; ++i) {
+                        const float v = __uint_as_float(rr[i]);
+                        if (v > thr && c0 + i < lim) {
+                            rs[cnt] = v;
+                            ri[cnt] = (uint32_t)(n0 + c0 + i);
+                            ++cnt;
+                        }
                     }
-                }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float v = __uint_as_float(rb[j]);
-                    if (v > thr && cb + 32 + j < lim) {
-                        rs[cnt] = v;
-                        ri[cnt] = (uint32_t)(n0 + cb + 32 + j);
-                        ++cnt;
-                    }
+                };
+                take(r0, cb);
+                take(r1, cb + 32);
+                if constexpr (kGW == 128) {
+                    take(r2, cb + 64);
+                    take(r3, cb + 96);
                 }
             }
             tc_fence_before();
@@ -549,18 +616,25 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
     }
 }
 
-int knn_tc_stages(int d) {
+// Halves of T per CTA: two while both halves' rows fit beside four stages.
+int knn_tc_halves(int d, bool tma) {
     const int nkc = (d + kKC - 1) / kKC;
-    const int budget = 225 * 1024 - nkc * (int)kChunkA;
-    int s = budget / (int)kChunkB;
+    return tma && nkc <= 4 ? 2 : 1;
+}
+
+int knn_tc_stages(int d, int mh) {
+    const int nkc = (d + kKC - 1) / kKC;
+    const int budget = 225 * 1024 - nkc * mh * (int)kChunkA;
+    int s = budget / (int)(mh == 2 ? KnnShape<2>::chunkB : KnnShape<1>::chunkB);
     return s > kMaxStages ? kMaxStages : s;
 }
 
 }  // namespace
 
-size_t knn_tc_smem_bytes(int d) {
+size_t knn_tc_smem_bytes(int d, int mh) {
     const int nkc = (d + kKC - 1) / kKC;
-    const size_t need = (size_t)nkc * kChunkA + (size_t)knn_tc_stages(d) * kChunkB + 1024;
+    const size_t need = (size_t)nkc * mh * kChunkA +
+                        (size_t)knn_tc_stages(d, mh) * (mh == 2 ? KnnShape<2>::chunkB : KnnShape<1>::chunkB) + 1024;
     return need < 120 * 1024 ? 120 * 1024 : need;  // one CTA per SM: it holds all 512 TMEM columns
 }
 
@@ -606,6 +680,10 @@ bool make_map(CUtensorMap *m, const __nv_bfloat16 *base, int64_t rows, int d, in
 #ifndef ROAR_KNN_TMA_DEFAULT
 #define ROAR_KNN_TMA_DEFAULT 1
 #endif
+static int knn_env_int(const char *name, int dflt) {
+    const char *e = std::getenv(name);
+    return e ? std::atoi(e) : dflt;
+}
 static bool knn_use_tma() {
     static const bool use = []() {
         const char *e = std::getenv("ROAR_KNN_TMA");
@@ -614,31 +692,54 @@ static bool knn_use_tma() {
     return use;
 }
 
+// T rows one full wave of the kNN kernel covers (one CTA per SM).
+int64_t knn_tc_wave_rows(int d) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    cudaGetLastError();
+    const bool want = knn_use_tma() && (d % 8) == 0;
+    const int mh = knn_env_int("ROAR_KNN_HALVES", 0) == 1 ? 1 : knn_tc_halves(d, want);
+    return (int64_t)sms * kTM * mh;
+}
+
 // Candidates (best C per row, unsorted, 0xFFFFFFFF padded) of nt rows of T16
 // against X16 into cand [nt][C]; buf_s/buf_i are [nt][cap] scratch.
 cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloat16 *X16, int64_t n, int d,
                           int C, int cap, float *buf_s, uint32_t *buf_i, uint32_t *cand, int *err,
                           uint64_t wait_ns, cudaStream_t s) {
-    const int stages = knn_tc_stages(d);
-    // A cut must leave room for a whole tile: C + kTN <= kCap.
-    if (stages < 2 || cap != kCap || C < 1 || C + kTN > kCap) return cudaErrorInvalidValue;
-    const size_t smem = knn_tc_smem_bytes(d);
-    const int64_t blocks = (nt + kTM - 1) / kTM;
     alignas(64) CUtensorMap tmA, tmB;
     std::memset(&tmA, 0, sizeof tmA);
     std::memset(&tmB, 0, sizeof tmB);
-    const bool tma = knn_use_tma() && (d % 8) == 0 && make_map(&tmA, T16, nt, d, kTM) && make_map(&tmB, X16, n, d, kTN);
+    const bool want = knn_use_tma() && (d % 8) == 0;
+    int mh = knn_tc_halves(d, want);
+    static const int mh_env = knn_env_int("ROAR_KNN_HALVES", 0);
+    if (mh_env == 1) mh = 1;
+
+    const bool tma = want && make_map(&tmA, T16, nt, d, kTM) && make_map(&tmB, X16, n, d, 256 / mh);
+    if (!tma) mh = 1;   // tensor maps refused: the cp.async producers stage one half
+    const int tn = 256 / mh;
+    const int stages = knn_tc_stages(d, mh);
+    // A cut must leave room for a whole tile: C + tn <= kCap.
+    if (stages < 2 || cap != kCap || C < 1 || C + tn > kCap) return cudaErrorInvalidValue;
+    const size_t smem = knn_tc_smem_bytes(d, mh);
+    const int64_t blocks = (nt + kTM * mh - 1) / (kTM * mh);
     cudaError_t e;
-    if (tma) {
-        e = cudaFuncSetAttribute(knn_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (mh == 2) {
+        e = cudaFuncSetAttribute(knn_tc_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        knn_tc_kernel<true><<<(unsigned)blocks, kThreads, smem, s>>>(T16, nt, X16, n, d, stages, C, buf_s, buf_i,
-                                                                     cand, err, wait_ns, tmA, tmB);
+        knn_tc_kernel<true, 2><<<(unsigned)blocks, KnnShape<2>::threads, smem, s>>>(
+            T16, nt, X16, n, d, stages, C, buf_s, buf_i, cand, err, wait_ns, tmA, tmB);
+    } else if (tma) {
+        e = cudaFuncSetAttribute(knn_tc_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        knn_tc_kernel<true, 1><<<(unsigned)blocks, KnnShape<1>::threads, smem, s>>>(
+            T16, nt, X16, n, d, stages, C, buf_s, buf_i, cand, err, wait_ns, tmA, tmB);
     } else {
-        e = cudaFuncSetAttribute(knn_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(knn_tc_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        knn_tc_kernel<false><<<(unsigned)blocks, kThreads, smem, s>>>(T16, nt, X16, n, d, stages, C, buf_s, buf_i,
-                                                                      cand, err, wait_ns, tmA, tmB);
+        knn_tc_kernel<false, 1><<<(unsigned)blocks, KnnShape<1>::threads, smem, s>>>(
+            T16, nt, X16, n, d, stages, C, buf_s, buf_i, cand, err, wait_ns, tmA, tmB);
     }
     return cudaGetLastError();
 }

@@ -62,6 +62,34 @@ def test_knn_small_n_and_ragged():
         assert sorted(got[r].tolist()) == list(range(77))
 
 
+@pytest.mark.parametrize("d", [256, 264, 512])
+def test_knn_wide_rows(d):
+    """Both CTA shapes of the tensor-core kNN: two 128-row halves of T per CTA
+    sharing each X tile (d <= 256) and one half (d > 256), on ragged sizes;
+    returned distances exact in the fixed FP32 order, sets equal to FP64 brute
+    force up to FP32 near-ties."""
+    import torch
+
+    import paper_2408_08933_gb300 as pkg
+
+    rng = np.random.default_rng(d)
+    X = rng.standard_normal((2999, d)).astype(np.float32)
+    T = rng.standard_normal((517, d)).astype(np.float32)
+    ids, dist = pkg.knn(_cuda(T), _cuda(X), 50)
+    torch.cuda.synchronize()
+    ids = ids.cpu().numpy().view(np.uint32)
+    dist = dist.cpu().numpy()
+    ref, ref_d = oracle.knn_f64(T, X, 50)
+    for r in range(0, T.shape[0], 7):
+        assert np.all(np.diff(dist[r]) >= 0)
+        for j in (0, 49):
+            assert dist[r, j] == -oracle.dot_fixed(T[r], X[ids[r, j]])
+        d64 = -(X[ids[r]].astype(np.float64) @ T[r].astype(np.float64))
+        assert np.all(d64 <= ref_d[r, 49] + 1e-4)
+    hits = sum(len(set(ids[r]) & set(ref[r])) for r in range(T.shape[0]))
+    assert hits / (50 * T.shape[0]) >= 0.999
+
+
 def test_build_invariants_and_recall(tiny):
     import torch
 
