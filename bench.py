@@ -316,14 +316,13 @@ def _serve_rate(srv, Qpool, rate, duration, seed_tag):
             pending[rid] = (nq, int(ks[i]), t_arr[i], now)
             qoff += nq
             i += 1
-        for rid in list(pending):
+        for rid in srv.ready():
             nq, k, ta, tsub = pending[rid]
             r = srv.poll(rid, nq, k, timeout_ms=0, want_results=False)
-            if r is not None:
-                lats.append((tsub - ta) + r[0])
-                done_q += nq
-                t_last = time.perf_counter()
-                del pending[rid]
+            lats.append((tsub - ta) + r[0])
+            done_q += nq
+            t_last = time.perf_counter()
+            del pending[rid]
     span = max(1e-9, t_last - start)
     lats = np.asarray(lats)
     return {"offered_qps": rate, "achieved_qps": done_q / span, "requests": int(len(lats)),
@@ -478,11 +477,37 @@ def _serving_section(torch, pkg, rs, w, dev, Xd, adj, entry, Q, Qd, gt, dtype, l
     sw = _sweep(sidx, Qd, gt, torch, [50, 75, 100, 150, 200, 300, 400])
     L90, reached = _pick_L(sw)
     sidx.autotune(Qd, 10, 400, repeats=1)
-    srv = pkg.Server(sidx, k_max=100, L_max=400, ring_capacity=1 << 16, idle_ms=50)
     Qpool = rs.test_queries(rs.scaled(w, n_test=65536))
+    # The device's capacity for the same mix: the queries of a Poisson stream
+    # (each with its request's k and L) as one graph-captured uneven batch.
+    _, sz, ks, Ls = rs.poisson_requests(1e6, 1.0, seed_tag=299)
+    kq = np.repeat(ks, sz)[:len(Qpool)].astype(np.int32)
+    Lq = np.repeat(Ls, sz)[:len(Qpool)].astype(np.int32)
+    nb = len(kq)
+    Qb = torch.from_numpy(Qpool[:nb]).to(dev)
+    kbd, Lbd = torch.from_numpy(kq).to(dev), torch.from_numpy(Lq).to(dev)
+    bout = sidx.uneven_outputs(kq)
+    plan = sidx.plan_uneven(Qb, kbd, Lbd, 400, bout, longest_first=True)
+    for _ in range(2):
+        plan.launch()
+    torch.cuda.synchronize()
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_ev.record()
+    for _ in range(3):
+        plan.launch()
+    b_ev.record()
+    torch.cuda.synchronize()
+    bms = a_ev.elapsed_time(b_ev) / 3
+    batched = {"queries": nb, "ms_per_launch": bms, "qps": nb / (bms / 1e3),
+               "mean_visits": float(bout[3].double().mean()), "graph_captured": True}
+    plan.close()
+    del Qb, kbd, Lbd, bout
+    log(f"serving mix as one batch: {batched}")
+    srv = pkg.Server(sidx, k_max=100, L_max=400, ring_capacity=1 << 16, idle_ms=50)
     res = {"index": w.name, "base": f"{w.n}x{w.d}",
            "form": dtype if dtype == "f32" else f"{dtype} traversal + fp32 re-rank",
-           "requests": "Poisson arrivals; 1..256 queries; k in {10,100}; L in [50,400]", "rates": []}
+           "requests": "Poisson arrivals; 1..256 queries; k in {10,100}; L in [50,400]",
+           "same_mix_batched": batched, "rates": []}
     for j, rate in enumerate((1e4, 3e4, 1e5, 3e5, 1e6)):
         res["rates"].append(_serve_rate(srv, Qpool, rate, 1.0, 200 + j))
         log(f"serving {res['rates'][-1]}")

@@ -320,9 +320,11 @@ roar_status roar_search_noalloc(int64_t n, int32_t d, const float *base_f32, con
  * Serving loop (continuous batching; no counterpart in the paper, whose
  * search runs one query at a time, Sec. 5.1). A server keeps the handle's
  * index resident and runs one persistent search kernel whose teams take
- * queries from a ring of slots in mapped pinned host memory as they are
- * published, so requests that arrive while others run start as soon as a
- * team is free. Every query is the beam search of roar_search with its
+ * queries from a ring of slots in device memory as they are published, so
+ * requests that arrive while others run start as soon as a team is free.
+ * Queries, results and the publish / done marks move between host and device
+ * by copies (pinned staging of the ring's size on the host), never through
+ * host memory the kernel touches. Every query is the beam search of roar_search with its
  * request's k and L, bit-identical to searching it alone.
  * Admission, by memory: a query at (k, L) is charged
  *   4 d + 8 k + 24          its ring slot at its own k (query, results, counters)
@@ -361,6 +363,13 @@ roar_status roar_server_submit(roar_server *srv, const float *q_host, int32_t nq
  */
 roar_status roar_server_poll(roar_server *srv, uint64_t request_id, int32_t timeout_ms, uint32_t *ids,
                              float *dist, uint32_t *visits, int32_t *qstatus, double *latency_s);
+
+/*
+ * The ids of up to cap requests that are complete and not yet released
+ * (oldest first) into ids (host [cap]); *n gets how many. A client polls
+ * these instead of every request in flight. Errors: ROAR_EINVAL.
+ */
+roar_status roar_server_ready(roar_server *srv, uint64_t *ids, int32_t cap, int32_t *n);
 
 /* out[10]: ring capacity, queries submitted, completed, released, kernel
  * launches, CTAs per launch, warps per team, kernel running (0/1), bytes

@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
     L.roar_server_poll.restype = ctypes.c_int
     L.roar_server_stats.argtypes = [P, P]
     L.roar_server_stats.restype = ctypes.c_int
+    L.roar_server_ready.argtypes = [P, P, i32, ctypes.POINTER(i32)]
+    L.roar_server_ready.restype = ctypes.c_int
     L.roar_server_destroy.argtypes = [P]
     L.roar_server_destroy.restype = None
     L.roar_quantize.argtypes = [P, i64, i32, ctypes.c_int, P, P, P]
@@ -237,6 +239,16 @@ def roar_server_poll(srv, request_id, timeout_ms, ids=None, dist=None, visits=No
         return None
     _check(st, "roar_server_poll")
     return lat.value
+
+
+def roar_server_ready(srv, cap=4096):
+    """Ids of complete, unreleased requests (oldest first), at most cap."""
+    import numpy as np
+
+    ids = np.empty(cap, dtype=np.uint64)
+    n = ctypes.c_int32()
+    _check(lib().roar_server_ready(srv, ids.ctypes.data, cap, ctypes.byref(n)), "roar_server_ready")
+    return ids[:n.value].tolist()
 
 
 def roar_server_stats(srv):
@@ -622,6 +634,10 @@ class Server:
             return None if lat is None else (lat, ids, dist, vis, st)
         lat = roar_server_poll(self.handle, rid, timeout_ms)
         return None if lat is None else (lat, None, None, None, None)
+
+    def ready(self, cap=4096):
+        """Ids of the requests that are complete and not yet polled."""
+        return roar_server_ready(self.handle, cap)
 
     def stats(self):
         return roar_server_stats(self.handle)

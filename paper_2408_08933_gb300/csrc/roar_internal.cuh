@@ -69,12 +69,15 @@ struct SearchArgs {
     uint32_t *vlog;          // per-warp-slot log of the ids set in the bitmap, vlog_cap each
     int32_t vlog_cap;
     unsigned int *work;      // next unclaimed query (reset per launch)
-    // Serving ring (all null for batch launches): queries, k, L and result
-    // slots are indexed by slot = sequence % ring_cap.
-    const volatile unsigned long long *ring_tail;  // mapped host: requests published so far
-    unsigned long long *ring_head;                 // device: requests claimed so far
-    volatile uint32_t *ring_done;                  // mapped host: per slot, low 32 bits of seq + 1 when done
-    const volatile int *ring_stop;                 // mapped host: nonzero asks the kernel to exit
+    // Serving ring in device memory (all null for batch launches): queries,
+    // k, L and result slots are indexed by slot = sequence % ring_cap.
+    const float *ring_rec;                         // per slot: query (d floats), k, L (int32), padding
+    int32_t ring_stride;                           // floats per record (a multiple of 4)
+    const uint32_t *ring_pub;                      // per slot, low 32 bits of seq + 1 once published
+    unsigned long long *ring_head;                 // tickets taken so far
+    unsigned long long *ring_orphan;               // per team slot: a ticket kept over an idle exit, or ~0
+    volatile uint32_t *ring_done;                  // per slot, low 32 bits of seq + 1 when done
+    const volatile int *ring_stop;                 // nonzero asks the kernel to exit
     int64_t ring_cap;
     int32_t ring_kmax;                             // result slots per ring entry
     uint32_t idle_polls;                           // empty polls (about 1 us apart) before exiting

@@ -540,29 +540,33 @@ beam_search_kernel(const SearchArgs a) {
         }
     };
 
-    const bool serving = a.ring_tail != nullptr;
+    const bool serving = a.ring_pub != nullptr;
     for (;;) {
         if (leader && lane == 0) {
             if (!serving) {
                 ctl[0] = (int)atomicAdd(a.work, 1u);
             } else {
-                // Claim the next published request; bounded idle polling.
+                // Take the next ticket (a sequence number) with one atomicAdd,
+                // or the ticket this team slot held when the last launch
+                // exited, and wait (bounded) for its slot's publish mark. A
+                // CAS loop on the head made every waiting team retry each
+                // claim, and under load the claims were the serving limit.
+                // On an idle exit the ticket is kept for the next launch.
                 long long got = -1;
+                unsigned long long t = *reinterpret_cast<volatile unsigned long long *>(a.ring_orphan + slot);
+                if (t == ~0ull) t = atomicAdd(a.ring_head, 1ull);
+                else a.ring_orphan[slot] = ~0ull;
                 for (uint32_t spin = 0;; ++spin) {
                     if (*a.ring_stop) break;
-                    const unsigned long long h = *reinterpret_cast<volatile unsigned long long *>(a.ring_head);
-                    const unsigned long long t = *a.ring_tail;
-                    if (h < t) {
-                        if (atomicCAS(a.ring_head, h, h + 1) == h) {
-                            got = (long long)h;
-                            break;
-                        }
-                        continue;
+                    if (__ldcg(a.ring_pub + (t % (unsigned long long)a.ring_cap)) == (uint32_t)(t + 1)) {
+                        got = (long long)t;
+                        break;
                     }
                     if (spin >= a.idle_polls) break;
                     __nanosleep(1000);
                 }
-                __threadfence_system();  // request data was published before the tail
+                if (got < 0) a.ring_orphan[slot] = t;
+                __threadfence();  // the slot's data was written before its publish mark
                 ctl[0] = (int)(got & 0xFFFFFFFF);
                 ctl[3] = (int)(got >> 32);
             }
@@ -578,9 +582,11 @@ beam_search_kernel(const SearchArgs a) {
             if (claim < 0) break;
             qi = claim % a.ring_cap;
         }
-        // Serving inputs change between requests in a slot: read them coherently.
-        const int k = serving ? *(const volatile int32_t *)(a.k_arr + qi) : (a.k_arr ? a.k_arr[qi] : a.k);
-        const int L = serving ? *(const volatile int32_t *)(a.L_arr + qi) : (a.L_arr ? a.L_arr[qi] : a.L);
+        // A serving slot is one record (query, then k and L), rewritten when
+        // the ring wraps: read it from L2.
+        const float *rec = serving ? a.ring_rec + qi * (int64_t)a.ring_stride : nullptr;
+        const int k = serving ? __ldcg(reinterpret_cast<const int *>(rec + d)) : (a.k_arr ? a.k_arr[qi] : a.k);
+        const int L = serving ? __ldcg(reinterpret_cast<const int *>(rec + d) + 1) : (a.L_arr ? a.L_arr[qi] : a.L);
         const int64_t ooff = serving ? qi * (int64_t)a.ring_kmax : (a.out_off ? a.out_off[qi] : qi * (int64_t)k);
         if (L < 1 || L > lcap || k < 1 || k > L || (serving && k > a.ring_kmax)) {  // bad (k, L): report, skip
             if (leader && lane == 0) {
@@ -588,7 +594,7 @@ beam_search_kernel(const SearchArgs a) {
                 if (a.hops) a.hops[qi] = 0;
                 if (a.qstatus) a.qstatus[qi] = ROAR_EINVAL;
                 if (serving) {
-                    __threadfence_system();
+                    __threadfence();
                     a.ring_done[qi] = (uint32_t)(claim + 1);
                 }
             }
@@ -596,11 +602,11 @@ beam_search_kernel(const SearchArgs a) {
         }
 
         float4 qr[NCH];
-        const float4 *q4 = reinterpret_cast<const float4 *>(a.q + qi * (int64_t)d);
+        const float4 *q4 = reinterpret_cast<const float4 *>(serving ? rec : a.q + qi * (int64_t)d);
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
             const int ch = lane + 32 * c;
-            qr[c] = ch < d4 ? (serving ? __ldcv(q4 + ch) : __ldg(q4 + ch)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            qr[c] = ch < d4 ? (serving ? __ldcg(q4 + ch) : __ldg(q4 + ch)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         // Leader-only search state.
         int64_t bi_j = 0, bi_end = 0;   // BI: query nodes of the base node being expanded
@@ -945,14 +951,13 @@ beam_search_kernel(const SearchArgs a) {
             }
         }
         if (leader) {
-            if (serving) __threadfence_system();  // every lane's result writes, before the done mark
-            __syncwarp();
+            __syncwarp();  // orders every lane's result writes before lane 0's fence below
             if (lane == 0) {
                 if (a.visits) a.visits[qi] = visits;
                 if (a.hops) a.hops[qi] = hops;
                 if (a.qstatus) a.qstatus[qi] = overflow ? ROAR_EOVERFLOW : (bad ? ROAR_EINVAL : ROAR_OK);
-                if (serving) {  // results are visible to the host before the done mark
-                    __threadfence_system();
+                if (serving) {  // the results (cumulative over the warp) before the done mark
+                    __threadfence();
                     a.ring_done[qi] = (uint32_t)(claim + 1);
                 }
             }

@@ -179,3 +179,28 @@ def test_admission_by_memory(tiny, two_handles):
     for rid, (q, L) in {a: (Q[:8], 50), c: (Q[16:24], 50), b: (Q[8:16], 400)}.items():
         assert np.array_equal(got[rid][1], run(ref, q, 10, L)[0])
     srv.close()
+
+
+def test_ready_lists_completed_requests(tiny, two_handles):
+    """ready() names exactly the complete, unpolled requests, oldest first;
+    polling them releases them."""
+    serve, ref = two_handles
+    srv = pkg.Server(serve, k_max=10, L_max=100, ring_capacity=1024, idle_ms=20)
+    Q = tiny["Q"]
+    rids = [srv.submit(Q[8 * i:8 * i + 8], 10, 50) for i in range(6)]
+    assert all(r is not None for r in rids)
+    t_end = time.time() + 10
+    while time.time() < t_end and len(srv.ready()) < len(rids):
+        time.sleep(0.001)
+    ready = srv.ready()
+    assert ready == sorted(rids)
+    for rid in ready[:3]:
+        r = srv.poll(rid, 8, 10, timeout_ms=0)
+        i = rids.index(rid)
+        assert np.array_equal(r[1], run(ref, Q[8 * i:8 * i + 8], 10, 50)[0])
+    assert srv.ready() == sorted(rids)[3:]
+    assert srv.ready(cap=1) == sorted(rids)[3:4]
+    for rid in srv.ready():
+        srv.poll(rid, 8, 10, timeout_ms=0)
+    assert srv.ready() == []
+    srv.close()
