@@ -80,7 +80,8 @@ struct SearchArgs {
     const volatile int *ring_stop;                 // nonzero asks the kernel to exit
     int64_t ring_cap;
     int32_t ring_kmax;                             // result slots per ring entry
-    uint32_t idle_polls;                           // empty polls (about 1 us apart) before exiting
+    uint32_t idle_polls;                           // microseconds without a served ticket before the kernel exits
+    unsigned long long *ring_clock;                // [0] global time of the last ticket served, [1] closing flag
     uint32_t *ids;
     float *dist;
     uint32_t *visits;

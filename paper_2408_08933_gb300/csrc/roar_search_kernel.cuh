@@ -27,6 +27,13 @@
 
 namespace roar {
 
+// Global nanosecond timer (the serving loop's idle clock).
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
@@ -541,6 +548,7 @@ beam_search_kernel(const SearchArgs a) {
     };
 
     const bool serving = a.ring_pub != nullptr;
+    const unsigned long long t_team0 = serving ? now_ns() : 0ull;   // idle floor (serving)
     for (;;) {
         if (leader && lane == 0) {
             if (!serving) {
@@ -551,18 +559,35 @@ beam_search_kernel(const SearchArgs a) {
                 // exited, and wait (bounded) for its slot's publish mark. A
                 // CAS loop on the head made every waiting team retry each
                 // claim, and under load the claims were the serving limit.
-                // On an idle exit the ticket is kept for the next launch.
+                // Idle exit is one decision for the whole kernel: a team gives
+                // up only when no team has been given a published ticket for
+                // idle_polls microseconds (ring_clock[0], the global time of
+                // the last one; a team's own start is the floor), and then
+                // raises ring_clock[1] so that the others stop waiting too.
+                // Its ticket is kept for the next launch; with exits per team,
+                // a ticket kept by an exited team while others ran waited for
+                // the whole kernel to time out.
                 long long got = -1;
                 unsigned long long t = *reinterpret_cast<volatile unsigned long long *>(a.ring_orphan + slot);
                 if (t == ~0ull) t = atomicAdd(a.ring_head, 1ull);
                 else a.ring_orphan[slot] = ~0ull;
+                const unsigned long long idle_ns = 1000ull * a.idle_polls;
+                volatile unsigned long long *clk = a.ring_clock;
                 for (uint32_t spin = 0;; ++spin) {
                     if (*a.ring_stop) break;
                     if (__ldcg(a.ring_pub + (t % (unsigned long long)a.ring_cap)) == (uint32_t)(t + 1)) {
                         got = (long long)t;
+                        clk[0] = now_ns();
                         break;
                     }
-                    if (spin >= a.idle_polls) break;
+                    if ((spin & 15) == 0) {
+                        if (clk[1]) break;
+                        const unsigned long long now = now_ns(), last = clk[0];
+                        if (now > (last > t_team0 ? last : t_team0) + idle_ns) {
+                            clk[1] = 1ull;
+                            break;
+                        }
+                    }
                     __nanosleep(1000);
                 }
                 if (got < 0) a.ring_orphan[slot] = t;

@@ -15,7 +15,8 @@
 //   - the kernel's teams take tickets (sequence numbers) in order with an
 //     atomicAdd on a device head counter, wait for the ticket's slot to be
 //     published, search, write the results into the slot and then the slot's
-//     done mark (a team that exits idle keeps its ticket for the next launch);
+//     done mark; when no ticket has been served for idle_ms the whole kernel
+//     exits, each team keeping its ticket for the next launch;
 //   - a host poller thread copies the done marks of the slots in flight to a
 //     pinned shadow, timestamps completions and relaunches the kernel when
 //     work is pending but the kernel has exited (its teams exit after a
@@ -92,6 +93,7 @@ struct roar_server {
     int *stop_d = nullptr;
     unsigned long long *head_dev = nullptr;
     unsigned long long *orphan_d = nullptr;   // per team slot (see the kernel's claim)
+    unsigned long long *clock_d = nullptr;    // the kernel's idle clock and closing flag
     // pinned host staging (submit) and the poller's shadow of the done marks
     float *rec_h = nullptr;
     uint32_t *pub_h = nullptr, *done_h = nullptr;
@@ -140,7 +142,9 @@ bool kernel_running(roar_server *s) {
 }
 
 roar_status launch_locked(roar_server *s) {
-    cudaError_t e = launch_search(s->args, s->blocks, s->tw, s->stream);
+    // A new launch starts with the idle clock cleared and not closing.
+    cudaError_t e = cudaMemsetAsync(s->clock_d, 0, 2 * sizeof(unsigned long long), s->stream);
+    if (e == cudaSuccess) e = launch_search(s->args, s->blocks, s->tw, s->stream);
     if (e == cudaSuccess) e = cudaEventRecord(s->ev_end, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "roar_server: launch");
     s->launched = true;
@@ -298,6 +302,7 @@ extern "C" roar_status roar_server_create(roar_index *idx, const roar_server_cfg
     const size_t team_slots = (size_t)s->blocks * (size_t)teams_per_block(s->tw);
     if (e == cudaSuccess) e = dev_alloc(&s->orphan_d, team_slots);
     if (e == cudaSuccess) e = cudaMemset(s->orphan_d, 0xFF, team_slots * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_alloc(&s->clock_d, 2);
     if (e == cudaSuccess) e = host_pinned(&s->rec_h, R * s->stride);
     if (e == cudaSuccess) e = host_pinned(&s->pub_h, R);
     if (e == cudaSuccess) e = host_pinned(&s->done_h, R);
@@ -330,6 +335,7 @@ extern "C" roar_status roar_server_create(roar_index *idx, const roar_server_cfg
     a.ring_pub = s->pub_d;
     a.ring_head = s->head_dev;
     a.ring_orphan = s->orphan_d;
+    a.ring_clock = s->clock_d;
     a.ring_done = s->done_d;
     a.ring_stop = s->stop_d;
     a.ring_cap = s->R;
@@ -509,6 +515,7 @@ extern "C" void roar_server_destroy(roar_server *s) {
     cudaFree(s->stop_d);
     cudaFree(s->head_dev);
     cudaFree(s->orphan_d);
+    cudaFree(s->clock_d);
     cudaFreeHost(s->rec_h);
     cudaFreeHost(s->pub_h);
     cudaFreeHost(s->done_h);
