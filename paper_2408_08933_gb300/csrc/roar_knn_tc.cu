@@ -616,10 +616,27 @@ knn_tc_kernel(const __nv_bfloat16 *__restrict__ T, int64_t nt, const __nv_bfloat
     }
 }
 
-// Halves of T per CTA: two while both halves' rows fit beside four stages.
-int knn_tc_halves(int d, bool tma) {
+// Halves of T per CTA: two while both halves' rows fit beside four stages,
+// unless one-half CTAs finish nt rows sooner. Every CTA sweeps all of X, a
+// two-half CTA in about twice the time (measured 0.55 of it for one half);
+// so a launch takes ceil(nt / (sms * 256)) two-half sweeps or
+// ceil(nt / (sms * 128)) one-half ones (a 14,336-row remainder: one sweep of
+// either, the one-half one the shorter).
+int knn_tc_halves(int d, bool tma, int64_t nt, int sms) {
     const int nkc = (d + kKC - 1) / kKC;
-    return tma && nkc <= 4 ? 2 : 1;
+    if (!tma || nkc > 4) return 1;
+    if (nt <= 0 || sms <= 0) return 2;
+    const int64_t w2 = (nt + (int64_t)sms * 2 * kTM - 1) / ((int64_t)sms * 2 * kTM);
+    const int64_t w1 = (nt + (int64_t)sms * kTM - 1) / ((int64_t)sms * kTM);
+    return 100 * w2 <= 55 * w1 ? 2 : 1;
+}
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    cudaGetLastError();
+    return sms;
 }
 
 int knn_tc_stages(int d, int mh) {
@@ -694,12 +711,9 @@ static bool knn_use_tma() {
 
 // T rows one full wave of the kNN kernel covers (one CTA per SM).
 int64_t knn_tc_wave_rows(int d) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        sms = 1;
-    cudaGetLastError();
+    const int sms = device_sms();
     const bool want = knn_use_tma() && (d % 8) == 0;
-    const int mh = knn_env_int("ROAR_KNN_HALVES", 0) == 1 ? 1 : knn_tc_halves(d, want);
+    const int mh = knn_env_int("ROAR_KNN_HALVES", 0) == 1 ? 1 : knn_tc_halves(d, want, 0, sms);   // whole waves of the wider shape
     return (int64_t)sms * kTM * mh;
 }
 
@@ -712,9 +726,11 @@ cudaError_t knn_tc_launch(const __nv_bfloat16 *T16, int64_t nt, const __nv_bfloa
     std::memset(&tmA, 0, sizeof tmA);
     std::memset(&tmB, 0, sizeof tmB);
     const bool want = knn_use_tma() && (d % 8) == 0;
-    int mh = knn_tc_halves(d, want);
-    static const int mh_env = knn_env_int("ROAR_KNN_HALVES", 0);
-    if (mh_env == 1) mh = 1;
+    int mh = knn_tc_halves(d, want, nt, device_sms());
+    // ROAR_KNN_HALVES=1 or 2 in the environment (read at every call) forces
+    // the shape where it can run; tests use it to cover both.
+    const int mh_env = knn_env_int("ROAR_KNN_HALVES", 0);
+    if (mh_env == 1 || (mh_env == 2 && knn_tc_halves(d, want, 0, 1) == 2)) mh = mh_env;
 
     const bool tma = want && make_map(&tmA, T16, nt, d, kTM) && make_map(&tmB, X16, n, d, 256 / mh);
     if (!tma) mh = 1;   // tensor maps refused: the cp.async producers stage one half

@@ -62,16 +62,17 @@ def test_knn_small_n_and_ragged():
         assert sorted(got[r].tolist()) == list(range(77))
 
 
-@pytest.mark.parametrize("d", [256, 264, 512])
-def test_knn_wide_rows(d):
+@pytest.mark.parametrize("d,halves", [(64, "2"), (256, "2"), (256, "1"), (256, ""), (264, ""), (512, "")])
+def test_knn_wide_rows(d, halves, monkeypatch):
     """Both CTA shapes of the tensor-core kNN: two 128-row halves of T per CTA
-    sharing each X tile (d <= 256) and one half (d > 256), on ragged sizes;
-    returned distances exact in the fixed FP32 order, sets equal to FP64 brute
-    force up to FP32 near-ties."""
+    sharing each X tile (d <= 256; forced here, small launches pick one half)
+    and one half, on ragged sizes; returned distances exact in the fixed FP32
+    order, sets equal to FP64 brute force up to FP32 near-ties."""
     import torch
 
     import paper_2408_08933_gb300 as pkg
 
+    monkeypatch.setenv("ROAR_KNN_HALVES", halves)
     rng = np.random.default_rng(d)
     X = rng.standard_normal((2999, d)).astype(np.float32)
     T = rng.standard_normal((517, d)).astype(np.float32)

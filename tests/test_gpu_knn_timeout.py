@@ -14,10 +14,13 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-def test_knn_wait_runs_out_then_recovers():
+@pytest.mark.parametrize("halves", ["1", "2"])
+def test_knn_wait_runs_out_then_recovers(halves, monkeypatch):
     import torch
 
     import paper_2408_08933_gb300 as pkg
+
+    monkeypatch.setenv("ROAR_KNN_HALVES", halves)   # both CTA shapes' abort paths
 
     rng = np.random.default_rng(11)
     X = rng.standard_normal((5000, 64)).astype(np.float32)
