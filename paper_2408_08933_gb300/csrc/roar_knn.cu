@@ -91,26 +91,51 @@ __global__ void rescore_kernel(const float *__restrict__ T, int64_t nt, const fl
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row = (int64_t)blockIdx.x * 4 + w;
     if (row >= nt) return;
-    const int d4 = d >> 2;
+    const int d4 = d >> 2;   // d <= 512: at most 4 chunks per lane
     const float4 *q4 = reinterpret_cast<const float4 *>(T + row * d);
-    for (int j = 0; j < C; ++j) {
-        const uint32_t u = cand[row * C + j];
-        float s = 0.0f;
-        if (u != 0xFFFFFFFFu) {
-            const float4 *x4 = reinterpret_cast<const float4 *>(X + (int64_t)u * d);
-            for (int ch = lane; ch < d4; ch += 32) {
-                const float4 a = __ldg(q4 + ch), b = __ldg(x4 + ch);
-                s = fmaf(a.x, b.x, s);
-                s = fmaf(a.y, b.y, s);
-                s = fmaf(a.z, b.z, s);
-                s = fmaf(a.w, b.w, s);
+    float4 qv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int ch = lane + 32 * c;
+        qv[c] = ch < d4 ? __ldg(q4 + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // G candidates at a time, so that their row loads are in flight together;
+    // each candidate's sum keeps its own order (chunks in increasing index).
+    constexpr int G = 4;
+    static_assert(C % G == 0, "candidates come in groups of G");
+    for (int j0 = 0; j0 < C; j0 += G) {
+        uint32_t u[G];
+        float s[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            u[g] = cand[row * C + j0 + g];
+            s[g] = 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int ch = lane + 32 * c;
+            if (ch >= d4) break;
+            float4 b[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                b[g] = u[g] != 0xFFFFFFFFu ? __ldg(reinterpret_cast<const float4 *>(X + (int64_t)u[g] * d) + ch)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                s[g] = fmaf(qv[c].x, b[g].x, s[g]);
+                s[g] = fmaf(qv[c].y, b[g].y, s[g]);
+                s[g] = fmaf(qv[c].z, b[g].z, s[g]);
+                s[g] = fmaf(qv[c].w, b[g].w, s[g]);
             }
         }
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) s = s + __shfl_xor_sync(kFull, s, o);
-        if (lane == 0) {
-            sd[w][j] = (u != 0xFFFFFFFFu) ? -s : __int_as_float(0x7f800000);
-            si[w][j] = u;
+        for (int g = 0; g < G; ++g) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) s[g] = s[g] + __shfl_xor_sync(kFull, s[g], o);
+            if (lane == 0) {
+                sd[w][j0 + g] = (u[g] != 0xFFFFFFFFu) ? -s[g] : __int_as_float(0x7f800000);
+                si[w][j0 + g] = u[g];
+            }
         }
     }
     __syncwarp();
