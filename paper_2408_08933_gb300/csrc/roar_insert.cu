@@ -21,8 +21,12 @@
 //   - rows are then applied in order on the host copy of the graph. Each
 //     graph row carries the sequence number of the last insertion that
 //     changed it; a search is still exact if no row it expanded changed after
-//     it ran, since a beam search is a function of the rows it expands. The
-//     first row whose search fails this test ends the window's apply; its
+//     it ran, since a beam search is a function of the rows it expands, or if
+//     the only changes are new neighbours appended to such rows that would not
+//     have entered the pool: each one's distance to the query is above the
+//     pool's L-th distance when the row was expanded (recorded by the search),
+//     so it would only have counted as a visit (the visits stay below the
+//     cap). The first row whose search fails this test ends the window's apply; its
 //     search is redone in the next window (on the graph with every earlier
 //     row applied, hence exact), and later rows keep theirs while they pass.
 //     A list N(v) is redone when N_out(q) grew since it was computed;
@@ -51,6 +55,22 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 double since(Clock::time_point t0) { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
+constexpr uint32_t kMaxVisits = 16384u;   // the insertion searches' visit cap
+
+// <a, b> in FP32: element i accumulates (fmaf, increasing i) into lane
+// (i >> 2) & 31 of 32 partial sums from +0, then s_l = s_l + s_(l xor o) for
+// o = 16, 8, 4, 2, 1; lane 0 is the result (the search kernel's order).
+float dot_fixed_host(const float *a, const float *b, int d) {
+    float lane[32] = {0};
+    for (int i = 0; i < d; ++i) lane[(i >> 2) & 31] = std::fmaf(a[i], b[i], lane[(i >> 2) & 31]);
+    for (int o = 16; o >= 1; o >>= 1) {
+        float next[32];
+        for (int l = 0; l < 32; ++l) next[l] = lane[l] + lane[l ^ o];
+        std::memcpy(lane, next, sizeof lane);
+    }
+    return lane[0];
+}
 
 // (dist, id) total order of the search.
 __device__ __forceinline__ bool less_entry(float da, uint32_t ia, float db, uint32_t ib) {
@@ -147,19 +167,23 @@ struct Inserter {
     std::vector<std::vector<uint32_t>> inc_new;
     std::vector<int64_t> stamp;               // last insertion (sequence number) that changed the row
     std::vector<int64_t> rewrite;             // last insertion that rewrote it (set or re-pruned)
+    std::vector<int32_t> pos_seq;             // [n_total][R]: the insertion that appended the entry there
     std::vector<char> pend_mark, chg_mark;
     int64_t applied = 0;                      // rows inserted so far
     // window slots (row v lives in slot v % W)
     int TC = 0, CS = 0;
     std::vector<int64_t> sl_v, sl_snap, sl_q;
-    std::vector<uint32_t> sl_hops, sl_pool, sl_trace, sl_acq;
+    std::vector<uint32_t> sl_hops, sl_pool, sl_trace, sl_acq, sl_vis;
+    std::vector<float> sl_bound;
+    std::vector<int32_t> sl_st;
     std::vector<int32_t> sl_acq_n, sl_acq_from;
     std::vector<char> sl_acq_ok;
     // pending re-prunes and changed rows
     std::vector<int64_t> pend, chg;
     // device buffers
     float *dq = nullptr, *ddist = nullptr;
-    uint32_t *dids = nullptr, *dhops = nullptr, *dtrace = nullptr;
+    uint32_t *dids = nullptr, *dhops = nullptr, *dtrace = nullptr, *dvis = nullptr;
+    float *dbound = nullptr;
     int32_t *dst = nullptr;
     uint32_t *dxs = nullptr, *dcand = nullptr, *dout = nullptr, *drows = nullptr;
     int32_t *dnc = nullptr, *dcnt = nullptr;
@@ -190,9 +214,32 @@ struct Inserter {
         if (snap == applied) return true;
         if (sl_hops[slot] > (uint32_t)TC) return false;
         const uint32_t *tr = sl_trace.data() + (size_t)slot * TC;
-        for (uint32_t i = 0; i < sl_hops[slot]; ++i)
-            if (stamp[tr[i]] >= snap) return false;
-        return true;
+        const float *bd = sl_bound.data() + (size_t)slot * TC;
+        const float *xu = Xnew.data() + (size_t)(sl_v[slot] - n_old) * d;
+        constexpr int kSeen = 64;
+        uint32_t seen[kSeen];
+        int nseen = 0;
+        for (uint32_t i = 0; i < sl_hops[slot]; ++i) {
+            const uint32_t e = tr[i];
+            if (stamp[e] < snap) continue;
+            if (rewrite[e] >= snap) return false;
+            // Only appended to since the search: each new neighbour must stay
+            // out of the pool (distance above the bound), ties are refused.
+            for (int j = 0; j < R; ++j) {
+                if (pos_seq[(size_t)e * R + j] < snap) continue;
+                const uint32_t v = adj[(size_t)e * R + j];
+                const float dv = -dot_fixed_host(xu, Xnew.data() + (size_t)(v - n_old) * d, d);
+                if (!(dv > bd[i])) return false;
+                bool dup = false;
+                for (int t = 0; t < nseen; ++t) dup = dup || seen[t] == v;
+                if (!dup) {
+                    if (nseen == kSeen) return false;
+                    seen[nseen++] = v;
+                }
+            }
+        }
+        // The sequential search would have made these extra visits.
+        return nseen == 0 || (sl_st[slot] == ROAR_OK && (uint64_t)sl_vis[slot] + (uint64_t)nseen < kMaxVisits);
     }
 
     void mark_changed(int64_t r) {
@@ -385,14 +432,21 @@ struct Inserter {
         a.dist = ddist;
         a.hops = dhops;
         a.qstatus = dst;
+        a.visits = dvis;
         a.trace = dtrace;
+        a.trace_bound = dbound;
         a.trace_cap = TC;
         e = launch_search(a, blocks, tw_plan, s);
         if (e != cudaSuccess) return fail(e, "roar_insert: search launch");
-        std::vector<uint32_t> ids((size_t)m * L), hops((size_t)m), tr((size_t)m * TC);
+        std::vector<uint32_t> ids((size_t)m * L), hops((size_t)m), tr((size_t)m * TC), vis((size_t)m);
+        std::vector<float> bnd((size_t)m * TC);
+        std::vector<int32_t> st((size_t)m);
         e = cudaMemcpyAsync(ids.data(), dids, ids.size() * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hops.data(), dhops, hops.size() * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tr.data(), dtrace, tr.size() * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bnd.data(), dbound, bnd.size() * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vis.data(), dvis, vis.size() * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(st.data(), dst, st.size() * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(e, "roar_insert: search");
         for (int64_t i = 0; i < m; ++i) {
@@ -401,7 +455,11 @@ struct Inserter {
                       sl_pool.begin() + (size_t)slot * L);
             std::copy(tr.begin() + (size_t)i * TC, tr.begin() + (size_t)(i + 1) * TC,
                       sl_trace.begin() + (size_t)slot * TC);
+            std::copy(bnd.begin() + (size_t)i * TC, bnd.begin() + (size_t)(i + 1) * TC,
+                      sl_bound.begin() + (size_t)slot * TC);
             sl_hops[slot] = hops[i];
+            sl_vis[slot] = vis[i];
+            sl_st[slot] = st[i];
             sl_snap[slot] = applied;
             sl_q[slot] = -2;
             sl_acq_ok[slot] = 0;
@@ -433,6 +491,7 @@ struct Inserter {
             mark_changed(p);
             if (deg < R) {
                 rp[deg] = (uint32_t)v;
+                pos_seq[(size_t)p * R + deg] = (int32_t)applied;
                 continue;
             }
             if ((int64_t)pend.size() == acq_cap) {
@@ -490,6 +549,7 @@ struct Inserter {
         inc_new.assign((size_t)n_new, {});
         stamp.assign((size_t)n_total, -1);
         rewrite.assign((size_t)n_total, -1);
+        pos_seq.assign((size_t)n_total * R, -1);
         pend_mark.assign((size_t)n_total, 0);
         chg_mark.assign((size_t)n_total, 0);
         TC = 2 * L + 128;
@@ -502,6 +562,9 @@ struct Inserter {
         sl_hops.assign(W, 0);
         sl_pool.assign((size_t)W * L, ROAR_NONE_ID);
         sl_trace.assign((size_t)W * TC, 0);
+        sl_bound.assign((size_t)W * TC, 0.0f);
+        sl_vis.assign(W, 0);
+        sl_st.assign(W, 0);
         sl_acq.assign((size_t)W * M, ROAR_NONE_ID);
         sl_acq_n.assign(W, 0);
         sl_acq_from.assign(W, -1);
@@ -520,6 +583,8 @@ struct Inserter {
         if (e == cudaSuccess) e = dalloc(&dhops, (size_t)W);
         if (e == cudaSuccess) e = dalloc(&dst, (size_t)W);
         if (e == cudaSuccess) e = dalloc(&dtrace, (size_t)W * TC);
+        if (e == cudaSuccess) e = dalloc(&dbound, (size_t)W * TC);
+        if (e == cudaSuccess) e = dalloc(&dvis, (size_t)W);
         if (e == cudaSuccess) e = dalloc(&dxs, (size_t)acq_cap);
         if (e == cudaSuccess) e = dalloc(&dcand, (size_t)acq_cap * CS);
         if (e == cudaSuccess) e = dalloc(&dnc, (size_t)acq_cap);
@@ -540,7 +605,7 @@ struct Inserter {
         e = cudaMemcpyAsync(dT, T, (size_t)nt * d * 4, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return fail(e, "roar_insert: training queries");
         roar_status rc = roar_index_create(n_total, d, X_dev, ROAR_F32, nullptr, nullptr, adj_dev, R, entry,
-                                           16384u, &gi);
+                                           kMaxVisits, &gi);
         if (rc != ROAR_OK) return rc;
         stats[6] = since(t_setup);
         std::vector<int> need, acq;
@@ -627,6 +692,8 @@ struct Inserter {
         cudaFree(dhops);
         cudaFree(dst);
         cudaFree(dtrace);
+        cudaFree(dbound);
+        cudaFree(dvis);
         cudaFree(dxs);
         cudaFree(dcand);
         cudaFree(dnc);

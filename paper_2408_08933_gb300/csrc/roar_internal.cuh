@@ -95,8 +95,10 @@ struct SearchArgs {
     int64_t bi_nt;
     // Optional expansion trace (batch launches, null otherwise): the first
     // trace_cap nodes a query expands, in order, at trace[qi * trace_cap ..];
-    // `hops` tells how many there were.
+    // `hops` tells how many there were. trace_bound (optional) gets, for each,
+    // the pool's L-th distance when it was expanded (+inf while not full).
     uint32_t *trace;
+    float *trace_bound;
     int32_t trace_cap;
 };
 

@@ -707,8 +707,13 @@ beam_search_kernel(const SearchArgs a) {
                         __syncwarp();
                         if (lane == 0) pi[sel] = v | kChecked;
                         ++hops;
-                        if (a.trace && lane == 0 && hops <= (uint32_t)a.trace_cap)
+                        if (a.trace && lane == 0 && hops <= (uint32_t)a.trace_cap) {
                             a.trace[qi * (int64_t)a.trace_cap + hops - 1] = v;
+                            // the pool's L-th distance as this node is expanded (+inf while not full)
+                            if (a.trace_bound)
+                                a.trace_bound[qi * (int64_t)a.trace_cap + hops - 1] =
+                                    size >= L ? pd[L - 1] : __int_as_float(0x7f800000);
+                        }
                         cursor = sel + 1;
                         if constexpr (BI) {
                             bi_j = a.bi_off[v];
