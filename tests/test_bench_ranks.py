@@ -49,3 +49,17 @@ def test_max_over_ranks_single_process():
     import bench
 
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun the reference arm (the CPU oracle) runs on rank 0 only;
+    every other rank exits 0 at once, printing nothing and touching no GPU."""
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
