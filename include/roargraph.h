@@ -508,12 +508,14 @@ roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const flo
  * room. All decisions use FP32 distances in the search's fixed summation
  * order.
  * The rows are processed in windows of `window` rows: their searches run in
- * one launch on the graph as it stands and record the nodes they expand; rows
- * are then applied in order while no node a row's search expanded has changed
- * since that search ran (then the search is the one the sequential order
- * runs); the first row that fails is searched again in the next window. So
- * the result never depends on `window`; window = 1 is the plain sequential
- * order.
+ * one launch on the graph as it stands and record the nodes they expand (and
+ * the pool's L-th distance at each); rows are then applied in order while the
+ * search is still the one the sequential order runs: no node it expanded has
+ * changed since, or those nodes only gained neighbours farther from the query
+ * than that bound (which would not have entered the pool) without the visits
+ * reaching the cap. The first row that fails is searched again in the next
+ * window. So the result never depends on `window`; window = 1 is the plain
+ * sequential order.
  *   X_dev        device [n_total][d] FP32 rows (the new rows already written).
  *   adj_dev      device [n_total][R] graph; rows >= n_old must be empty
  *                (ROAR_NONE_ID); updated in place. R <= 64, 1 <= M <= R.
@@ -534,8 +536,9 @@ roar_status roar_build_index(const float *X_dev, int64_t n, int32_t d, const flo
  *                stopped at a search that expanded a rewritten row, and
  *                those where every changed row it expanded was only appended
  *                to.
- * Synchronises `stream`. Uses about n_total * (R * 4 + 48) bytes of host
- * memory plus the connection lists, and a device copy of T_host. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
+ * Synchronises `stream`. Uses about n_total * (R * 8 + 48) bytes of host
+ * memory (the graph and, per entry, the insertion that appended it) plus the
+ * connection lists, and a device copy of T_host. Errors: ROAR_EINVAL, ROAR_ENOMEM, ROAR_ECUDA.
  */
 roar_status roar_insert(const float *X_dev, int64_t n_total, int32_t d, uint32_t *adj_dev, int32_t R,
                         uint32_t entry, int64_t n_old, const float *T_host, int64_t nt,
